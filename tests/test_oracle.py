@@ -55,6 +55,28 @@ def test_spline_matches_scipy_not_a_knot(orc, K):
     assert np.allclose(coef[:, 3], ref.c[0], rtol=1e-9, atol=1e-9 * np.max(np.abs(ref.c[0])))
 
 
+def test_spline_segment_rule_on_uneven_knots(orc):
+    """Every segment is used for its own interval, including the last one, when the
+    knots are far from log-spaced (the log-spaced first guess is then wrong)."""
+    from scipy.interpolate import CubicSpline
+
+    K = 40
+    for x in (1e-3 + np.geomspace(1e-7, 1e-1, K),          # clustered at the lower end
+              np.sort(1e-1 - np.geomspace(1e-5, 9e-2, K))):  # clustered at the upper end
+        _check_all_segments(orc, x, CubicSpline)
+
+
+def _check_all_segments(orc, x, CubicSpline):
+    K = x.size
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(K)
+    coef = orc.spline(x, y)
+    mids = 0.5 * (x[1:] + x[:-1])
+    f = np.concatenate([mids, x])
+    ref = CubicSpline(x, y, bc_type="not-a-knot")(f)
+    assert np.max(np.abs(orc.spline_eval(x, coef, f) - ref)) < 1e-10
+
+
 # ----------------------------------------------------------------------------- harmonics
 
 def _ylm_table(l, m, th, ph):
