@@ -1,0 +1,151 @@
+/*
+ * lisa_like.h -- C ABI of liblisalike.so: the batched LISA log-likelihood for
+ * massive-black-hole-binary templates (Katz, Marsat, Chua, Babak & Larson 2020),
+ * computed on one GB300 GPU.
+ *
+ * What one call computes (Sec. II and II.A of the paper), for every walker b:
+ *   1. the harmonic amplitude A_lm(f) and phase phi_lm(f) of Eq. (5) on K
+ *      log-spaced knots spanning the mode's band; t_lm(f) of Eq. (6) and the cut
+ *      where t_lm(f) < 0;
+ *   2. the TDI A/E/T transfer T(f, t_lm(f)) of Eqs. (7)-(10) at those knots;
+ *   3. not-a-knot cubic splines of A, phi and T onto the dense grid f_j = f0 + j df;
+ *   4. the sum over modes of T A e^{i(phi - 2 pi f t_coal)} (never stored);
+ *   5. <d|h> and <h|h> of Eqs. (3) and (11), and ln L = <d|h> - <h|h>/2 - <d|d>/2
+ *      of Eq. (2).
+ * The waveform and response coefficients are stand-ins of the paper's functional
+ * forms (the paper defers the fits to cited work); see the project design notes.
+ *
+ * Conventions used by every entry point:
+ *   - Parameters are double[B][11] rows in the paper's order (Sec. II):
+ *     M_T [M_sun, detector frame], q (<= 1), a1, a2, D_L [Gpc], phi_ref, iota,
+ *     lambda, beta, psi (SSB frame, rad), t_ref [s]; t_coal = t_ref + t0.
+ *   - Channel arrays are ordered A, E, T; complex values are interleaved (re, im).
+ *   - A walker with M_T <= 0, q outside (0, 1], |a_i| > 0.99, D_L <= 0 or any
+ *     non-finite entry gets ln L = -inf, <d|h> = <h|h> = 0; the status stays OK.
+ *   - A walker whose bands miss the grid has h = 0 and ln L = -<d|d>/2.
+ *   - On a non-OK status nothing is written to the outputs and
+ *     lisa_like_last_error() describes the failure.
+ *   - One handle per host thread; calls on one handle are serialised on its stream.
+ * Ownership: the library owns all device memory it allocates, until
+ * lisa_like_destroy(); inputs are copied; outputs are caller-allocated.
+ */
+#ifndef LISA_LIKE_H
+#define LISA_LIKE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lisa_like lisa_like_t;
+
+typedef enum {
+    LISA_OK = 0,
+    LISA_ERR_ARG = 1,     /* invalid argument (NULL, size, non-finite, bad mode ...) */
+    LISA_ERR_STATE = 2,   /* call out of order (e.g. loglike before set_data) */
+    LISA_ERR_CUDA = 3,    /* a CUDA runtime call failed */
+    LISA_ERR_OOM = 4,     /* device or pinned-host allocation failed */
+    LISA_ERR_TIMEOUT = 5  /* a bounded wait for the device gave up */
+} lisa_status;
+
+enum { LISA_PREC_FP64 = 0, LISA_PREC_SPLIT = 1 };
+
+#define LISA_NPAR 11
+#define LISA_MAX_MODES 6
+#define LISA_NSERIES 8
+
+typedef struct {
+    int n_modes;            /* 1..6 */
+    int modes[6][2];        /* (l,m) pairs from (2,2),(3,3),(4,4),(2,1),(3,2),(4,3) */
+    int n_knots;            /* K >= 4 knots per mode (not-a-knot needs 4); paper: ~2^10 */
+    int precision;          /* LISA_PREC_FP64 or LISA_PREC_SPLIT */
+    double t0_s;            /* t_coal = t_ref + t0 (Sec. II: t0 ~ 1 yr) */
+    int device;             /* CUDA device ordinal */
+    void *stream;           /* cudaStream_t to run on; NULL = the library creates one */
+    int max_batch;          /* largest B any call will use (device buffers sized for it) */
+    double timeout_s;       /* bound on host waits for the device; <= 0 means 60 s */
+} lisa_like_config;
+
+/* Fill *cfg with the defaults: six modes, K = 1024, FP64, t0 = 1 yr, device 0. */
+void lisa_like_default_config(lisa_like_config *cfg);
+
+/* Create a handle (Sec. II.A: everything that is done once before > 1e7 calls).
+ * Errors: LISA_ERR_ARG for a bad config, LISA_ERR_CUDA / LISA_ERR_OOM. */
+lisa_status lisa_like_create(const lisa_like_config *cfg, lisa_like_t **out);
+
+/* Upload the data stream and PSD once (Sec. II.A; the PSD of Sec. II).
+ *   f0 > 0, df > 0: the grid f_j = f0 + j df, j = 0 .. n_bins-1, 1 <= n_bins < 2^31.
+ *   d   host double[3][n_bins][2], the A, E, T data d~(f_j); NULL means d = 0.
+ *   psd host double[3][n_bins], one-sided S_n^{A,E,T}(f_j) > 0 and finite.
+ * Stores w = 4 df / S and w d on the device and computes <d|d> (FP64).
+ * Errors: LISA_ERR_ARG (NULL psd, non-finite value, S <= 0, bad grid). */
+lisa_status lisa_like_set_data(lisa_like_t *h, double f0, double df, int64_t n_bins,
+                               const double *d, const double *psd);
+
+/* Batched ln L for B host parameter rows (1 <= B <= max_batch); blocks until done.
+ *   params host double[B][11]; lnL host double[B]; dh, hh host double[B] or NULL.
+ * Errors: LISA_ERR_STATE before set_data, LISA_ERR_ARG, LISA_ERR_CUDA,
+ * LISA_ERR_TIMEOUT when the device does not finish within the configured bound. */
+lisa_status lisa_like_loglike(lisa_like_t *h, const double *params, int B, double *lnL,
+                              double *dh, double *hh);
+
+/* Same on device pointers, asynchronous on `stream` (NULL = the handle's stream).
+ *   d_params device double[B][11]; d_lnL device double[B]; d_dh, d_hh device or NULL.
+ * The call returns after enqueueing; the caller synchronises the stream. */
+lisa_status lisa_like_loglike_device(lisa_like_t *h, const double *d_params, int B,
+                                     double *d_lnL, double *d_dh, double *d_hh, void *stream);
+
+/* <d|d> of the uploaded data (Eqs. (3), (11)). */
+lisa_status lisa_like_data_inner(const lisa_like_t *h, double *dd);
+
+/* Dense template of one walker on the uploaded grid, materialised (for making
+ * injections and for element-wise checks): out host double[3][n_bins][2]. */
+lisa_status lisa_like_template(lisa_like_t *h, const double *params, double *out);
+
+/* Intermediate results of steps 1-2 for B host walkers, copied to host buffers:
+ *   band  int64_t[B][n_modes][3]: active flag, j_lo, j_hi (inclusive dense-bin range)
+ *   fedge double[B][n_modes][2]: f_lo, f_hi [Hz]
+ *   fk    double[B][n_modes][K]: knot frequencies
+ *   vals  double[B][n_modes][8][K]: A, phase (+ delay phase), Re/Im T^A, T^E, T^T
+ * Any output may be NULL. Requires set_data (the grid sets the bands). */
+lisa_status lisa_like_stage_knots(lisa_like_t *h, const double *params, int B, int64_t *band,
+                                  double *fedge, double *fk, double *vals);
+
+/* Spline coefficients of step 3 for B host walkers:
+ *   coef double[B][n_modes][K-1][8][4]; segment s, series q: c0 + c1 x + c2 x^2 + c3 x^3
+ *   with x = f - f_s. Requires set_data. */
+lisa_status lisa_like_stage_coeffs(lisa_like_t *h, const double *params, int B, double *coef);
+
+/* Luminosity distance [Gpc] at redshift z (flat LambdaCDM, H0 = 67.7, Om = 0.31),
+ * host-side helper for turning the redshifts of a workload into D_L. NaN if z < 0. */
+double lisa_dl_from_z(double z);
+
+/* Stand-in one-sided A/E/T PSD at f_j = f0 + j df, host helper: out host
+ * double[3][n_bins]. Returns LISA_ERR_ARG for a bad grid. */
+lisa_status lisa_psd_aet(double f0, double df, int64_t n_bins, double *out);
+
+/* Per-stage device timing with CUDA events (on = 1) of subsequent loglike and
+ * loglike_device calls, recorded on the stream each call runs on. */
+lisa_status lisa_like_set_profiling(lisa_like_t *h, int on);
+
+/* Sums of the per-stage device times [ms] of the calls profiled since the last read,
+ * ms[0] knots, ms[1] splines, ms[2] work planning, ms[3] fused dense ln L,
+ * ms[4] finishing; *n_calls receives the number of calls summed.  Waits (bounded by
+ * the configured timeout) for those calls, then clears the sums. */
+lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls);
+
+/* Number of kernel launches the last loglike / loglike_device call enqueued. */
+int lisa_like_last_launches(const lisa_like_t *h);
+
+/* Release every resource of the handle (NULL is allowed). */
+void lisa_like_destroy(lisa_like_t *h);
+
+/* Human-readable description of the last failure on this handle ("" if none);
+ * with h == NULL, the last failure of lisa_like_create on this thread. */
+const char *lisa_like_last_error(const lisa_like_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

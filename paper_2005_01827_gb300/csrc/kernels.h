@@ -1,0 +1,62 @@
+// kernels.h -- launchers of the device stages (internal to liblisalike.so).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lisa {
+
+// Device layout of one bin of the uploaded data: the FP64 dense kernel reads the
+// nine doubles w_A, w_E, w_T, (w d)_A re/im, (w d)_E re/im, (w d)_T re/im
+// (w = 4 df / S, Eqs. (3) and (11)); 72 bytes, 16-byte aligned rows of 2 bins.
+constexpr int kBinDoubles = 9;
+
+struct StageDims {
+    int B;       // walkers in this call
+    int L;       // modes
+    int K;       // knots per mode
+    int N;       // dense bins
+    double f0, df, t0;
+    int ml[6], mm[6];  // (l, m) of each mode
+};
+
+// Per-call device buffers (sized for max_batch by the host).
+struct StageBufs {
+    const double *params;  // [B][11]
+    int *valid;            // [B]
+    double *tc;            // [B]
+    int *band;             // [B][L][3]: active, j_lo, j_hi
+    double *fedge;         // [B][L][2]
+    double *fk;            // [B][L][K]
+    int *kb;               // [B][L][K]: first dense bin with f_j >= f_k
+    double *vals;          // [B][L][8][K]
+    double *mscratch;      // [B][L][8][K] second derivatives of the spline
+    double *coef;          // [B][L][K-1][8][4]
+    int *wrange;           // [B][2] union of the active mode ranges
+    int *item_start;       // [B+1] exclusive prefix of the dense work items
+    int *counter;          // dense work-queue counter
+    double *part;          // [items][2] per-item <d|h>, <h|h>
+};
+
+struct DenseTune {
+    int threads;     // threads per block
+    int per_thread;  // consecutive bins per thread
+    int blocks;      // persistent grid size
+};
+
+cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s);
+cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
+cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, cudaStream_t s);
+cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
+                             const DenseTune &t, cudaStream_t s);
+cudaError_t launch_finish(const StageDims &d, const StageBufs &b, double dd, double *lnL,
+                          double *dh, double *hh, cudaStream_t s);
+cudaError_t launch_template(const StageDims &d, const StageBufs &b, double *out,
+                            cudaStream_t s);
+cudaError_t launch_prep(const double *d, const double *psd, int N, double df, double *bins,
+                        double *ddpart, int *bad, cudaStream_t s);
+int prep_blocks(int N);
+
+// Largest number of dense work items a call with B walkers can produce.
+int64_t max_items(int B, int N, int tile_bins);
+
+}  // namespace lisa

@@ -1,0 +1,405 @@
+// stages.cu -- knot, spline, planning, finishing, data-preparation and template
+// kernels of the batched LISA likelihood (Katz et al. 2020, Sec. II.A).
+#include "kernels.h"
+#include "model.cuh"
+
+namespace lisa {
+
+// f_j = f0 + j df, rounded as a separate product and sum (no fused multiply-add) so
+// that band edges and knot-to-bin boundaries are decided exactly as written.
+__device__ __forceinline__ double bin_freq(double f0, double df, int j) {
+    return __dadd_rn(f0, __dmul_rn((double)j, df));
+}
+
+// ---------------------------------------------------------------------------- knots
+// One block per (walker, mode).  Thread 0 derives the walker constants and the band
+// (Sec. II: the cut where t_lm(f) < 0, and the ringdown cut); all threads then fill
+// the K log-spaced knots (Sec. II.A: ~2^10 points) with A, phase + delay, and T.
+__global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
+    const int wm = blockIdx.x;
+    const int w = wm / d.L, mi = wm % d.L;
+    const Mode md = {d.ml[mi], d.mm[mi]};
+    __shared__ Source src;
+    __shared__ Frame frame;
+    __shared__ cplx kp, kc;
+    __shared__ int active;
+    __shared__ double flo, fhi;
+
+    if (threadIdx.x == 0) {
+        const bool ok = make_source(b.params + (size_t)w * kNPar, d.t0, src);
+        int act = 0;
+        double lo = 0.0, hi = 0.0;
+        int jl = 0, jh = -1;
+        if (ok) {
+            make_frame(src, frame);
+            pol_weights(src, md, kp, kc);
+            const double fmn = d.f0;
+            const double fmx = bin_freq(d.f0, d.df, d.N - 1);
+            const double fcut = 0.5 * md.m * kXCut / src.M;
+            hi = fmx < fcut ? fmx : fcut;
+            if (hi > fmn * (1.0 + 1e-12)) {
+                act = 1;
+                if (mode_time(src, md, fmn) >= 0.0) {
+                    lo = fmn;
+                } else if (mode_time(src, md, hi) < 0.0) {
+                    act = 0;  // the mode ends before the observation starts
+                } else {
+                    double a = fmn, c = hi;
+                    for (int it = 0; it < 200 && c - a > 1e-14 * c; it++) {
+                        const double mid = 0.5 * (a + c);
+                        if (mode_time(src, md, mid) < 0.0)
+                            a = mid;
+                        else
+                            c = mid;
+                    }
+                    lo = c;
+                }
+                if (act && !(hi > lo * (1.0 + 1e-12))) act = 0;
+                if (act) {
+                    const double gl = ceil((lo - d.f0) / d.df - 1e-9);
+                    const double gh = floor((hi - d.f0) / d.df + 1e-9);
+                    jl = gl < 0.0 ? 0 : (int)gl;
+                    jh = gh > (double)(d.N - 1) ? d.N - 1 : (int)gh;
+                    if (jl > jh) act = 0;
+                }
+            }
+        }
+        if (!act) {
+            jl = 0;
+            jh = -1;
+        }
+        active = act;
+        flo = lo;
+        fhi = hi;
+        int *bd = b.band + (size_t)wm * 3;
+        bd[0] = act;
+        bd[1] = jl;
+        bd[2] = jh;
+        b.fedge[(size_t)wm * 2] = lo;
+        b.fedge[(size_t)wm * 2 + 1] = hi;
+        if (mi == 0) {
+            b.valid[w] = ok ? 1 : 0;
+            b.tc[w] = ok ? src.tc : 0.0;
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const int K = d.K;
+    const double r = log(fhi / flo);
+    double *fkm = b.fk + (size_t)wm * K;
+    int *kbm = b.kb + (size_t)wm * K;
+    double *vm = b.vals + (size_t)wm * kNSeries * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double f = (k == K - 1) ? fhi : flo * exp(r * (double)k / (double)(K - 1));
+        fkm[k] = f;
+        // first dense bin at or above this knot
+        double g = ceil((f - d.f0) / d.df);
+        int j = g <= 0.0 ? 0 : (g >= (double)d.N ? d.N : (int)g);
+        while (j > 0 && bin_freq(d.f0, d.df, j - 1) >= f) j--;
+        while (j < d.N && bin_freq(d.f0, d.df, j) < f) j++;
+        kbm[k] = j;
+        const double t = mode_time(src, md, f);
+        cplx T[3];
+        double dly;
+        tdi_transfer(frame, kp, kc, f, t, T, &dly);
+        vm[0 * K + k] = mode_amp(src, md, f);
+        vm[1 * K + k] = mode_phase(src, md, f) + dly;
+        vm[2 * K + k] = T[0].re;
+        vm[3 * K + k] = T[0].im;
+        vm[4 * K + k] = T[1].re;
+        vm[5 * K + k] = T[1].im;
+        vm[6 * K + k] = T[2].re;
+        vm[7 * K + k] = T[2].im;
+    }
+}
+
+cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    knot_kernel<<<d.B * d.L, 128, 0, s>>>(d, b);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- splines
+// One warp per (walker, mode).  Not-a-knot cubic splines (the Scipy-type tridiagonal
+// solve of Sec. II.A) for the 8 series share one matrix: lane 0 factorises it once,
+// lanes 0..7 each sweep one right-hand side, then all lanes emit the per-segment
+// coefficients.  Unknowns are the second derivatives M_1..M_{K-2}; not-a-knot
+// eliminates M_0 and M_{K-1}.
+__global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
+    extern __shared__ double sh[];
+    const int wm = blockIdx.x;
+    if (!b.band[(size_t)wm * 3]) return;
+    const int K = d.K, n = K;
+    double *hh = sh;            // [K-1] knot spacings
+    double *den = sh + K;       // [K] Thomas pivots
+    double *cpr = sh + 2 * K;   // [K] normalised super-diagonal
+    double *sub = sh + 3 * K;   // [K] sub-diagonal
+    const double *x = b.fk + (size_t)wm * K;
+    const double *y = b.vals + (size_t)wm * kNSeries * K;
+    double *Mv = b.mscratch + (size_t)wm * kNSeries * K;
+    const int lane = threadIdx.x;
+
+    for (int k = lane; k < n - 1; k += 32) hh[k] = x[k + 1] - x[k];
+    __syncwarp();
+    if (lane == 0) {
+        for (int i = 1; i <= n - 2; i++) {
+            double dia = 2.0 * (hh[i - 1] + hh[i]);
+            double sup = hh[i];
+            double sb = hh[i - 1];
+            if (i == 1) {
+                dia += hh[0] * (hh[0] + hh[1]) / hh[1];
+                sup -= hh[0] * hh[0] / hh[1];
+            }
+            if (i == n - 2) {
+                dia += hh[n - 2] * (hh[n - 3] + hh[n - 2]) / hh[n - 3];
+                sb -= hh[n - 2] * hh[n - 2] / hh[n - 3];
+            }
+            const double pv = (i == 1) ? dia : dia - sb * cpr[i - 1];
+            den[i] = pv;
+            cpr[i] = sup / pv;
+            sub[i] = sb;
+        }
+    }
+    __syncwarp();
+    if (lane < kNSeries) {
+        const double *yq = y + (size_t)lane * K;
+        double *Mq = Mv + (size_t)lane * K;
+        double prev = 0.0;
+        double dprev = (yq[1] - yq[0]) / hh[0];
+        for (int i = 1; i <= n - 2; i++) {
+            const double dcur = (yq[i + 1] - yq[i]) / hh[i];
+            const double rhs = 6.0 * (dcur - dprev);
+            dprev = dcur;
+            const double rp = (i == 1) ? rhs / den[1] : (rhs - sub[i] * prev) / den[i];
+            Mq[i] = rp;
+            prev = rp;
+        }
+        double nxt = Mq[n - 2];
+        for (int i = n - 3; i >= 1; i--) {
+            nxt = Mq[i] - cpr[i] * nxt;
+            Mq[i] = nxt;
+        }
+        Mq[0] = ((hh[0] + hh[1]) * Mq[1] - hh[0] * Mq[2]) / hh[1];
+        Mq[n - 1] = ((hh[n - 3] + hh[n - 2]) * Mq[n - 2] - hh[n - 2] * Mq[n - 3]) / hh[n - 3];
+    }
+    __syncwarp();
+    double *cm = b.coef + (size_t)wm * (K - 1) * 32;
+    for (int t = lane; t < (n - 1) * kNSeries; t += 32) {
+        const int sgm = t / kNSeries, q = t % kNSeries;
+        const double *yq = y + (size_t)q * K;
+        const double *Mq = Mv + (size_t)q * K;
+        const double h = hh[sgm];
+        const double m0 = Mq[sgm], m1 = Mq[sgm + 1];
+        double *c = cm + (size_t)sgm * 32 + q * 4;
+        c[0] = yq[sgm];
+        c[1] = (yq[sgm + 1] - yq[sgm]) / h - h * (2.0 * m0 + m1) / 6.0;
+        c[2] = 0.5 * m0;
+        c[3] = (m1 - m0) / (6.0 * h);
+    }
+}
+
+cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    const size_t smem = sizeof(double) * 4 * (size_t)d.K;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(spline_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    spline_kernel<<<d.B * d.L, 32, smem, s>>>(d, b);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- planning
+// Union of each walker's active mode ranges, split into tiles of tile_bins bins; the
+// exclusive prefix over walkers numbers the dense work items.  One block; also resets
+// the work-queue counter so the whole call needs no host round trip.
+__global__ void __launch_bounds__(1024) plan_kernel(StageDims d, StageBufs b, int tile_bins) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        carry = 0;
+        *b.counter = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < d.B; base += blockDim.x) {
+        const int w = base + tid;
+        int cnt = 0;
+        if (w < d.B) {
+            int lo = 0x7fffffff, hi = -1;
+            for (int mi = 0; mi < d.L; mi++) {
+                const int *bd = b.band + ((size_t)w * d.L + mi) * 3;
+                if (bd[0] && b.valid[w]) {
+                    lo = min(lo, bd[1]);
+                    hi = max(hi, bd[2]);
+                }
+            }
+            if (hi < lo) {
+                lo = 0;
+                hi = -1;
+            }
+            b.wrange[2 * w] = lo;
+            b.wrange[2 * w + 1] = hi;
+            cnt = hi >= lo ? (hi - lo + tile_bins) / tile_bins : 0;
+        }
+        // block-wide exclusive scan of cnt
+        int v = cnt;
+        const int lane = tid & 31, wid = tid >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) warp_tot[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + v - cnt;
+        if (w < d.B) b.item_start[w] = excl;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = excl + cnt;
+        __syncthreads();
+    }
+    if (tid == 0) b.item_start[d.B] = carry;
+}
+
+cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, cudaStream_t s) {
+    plan_kernel<<<1, 1024, 0, s>>>(d, b, tile_bins);
+    return cudaGetLastError();
+}
+
+int64_t max_items(int B, int N, int tile_bins) {
+    return (int64_t)B * (((int64_t)N + tile_bins - 1) / tile_bins + 1);
+}
+
+// ---------------------------------------------------------------------------- finish
+// ln L = <d|h> - <h|h>/2 - <d|d>/2 (Eq. (2)); per-walker sums of the dense items are
+// taken in item order, so results do not depend on which block ran which item.
+__global__ void finish_kernel(StageDims d, StageBufs b, double dd, double *lnL, double *dh,
+                              double *hh) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= d.B) return;
+    double a = 0.0, c = 0.0;
+    if (b.valid[w]) {
+        const int i0 = b.item_start[w], i1 = b.item_start[w + 1];
+        for (int i = i0; i < i1; i++) {
+            a += b.part[2 * (size_t)i];
+            c += b.part[2 * (size_t)i + 1];
+        }
+        lnL[w] = a - 0.5 * c - 0.5 * dd;
+    } else {
+        lnL[w] = -INFINITY;
+    }
+    if (dh) dh[w] = a;
+    if (hh) hh[w] = c;
+}
+
+cudaError_t launch_finish(const StageDims &d, const StageBufs &b, double dd, double *lnL,
+                          double *dh, double *hh, cudaStream_t s) {
+    finish_kernel<<<(d.B + 127) / 128, 128, 0, s>>>(d, b, dd, lnL, dh, hh);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- data prep
+// w = 4 df / S and w d per bin and channel (Eq. (3)), the partial sums of <d|d>, and a
+// flag for a non-positive or non-finite PSD value or a non-finite data value.
+__global__ void __launch_bounds__(256) prep_kernel(const double *d, const double *psd, int N,
+                                                   double df, double *bins, double *ddpart,
+                                                   int *bad) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        double *o = bins + (size_t)j * kBinDoubles;
+        for (int c = 0; c < 3; c++) {
+            const double S = psd[(size_t)c * N + j];
+            const double dr = d ? d[2 * ((size_t)c * N + j)] : 0.0;
+            const double di = d ? d[2 * ((size_t)c * N + j) + 1] : 0.0;
+            if (!(S > 0.0) || !isfinite(S) || !isfinite(dr) || !isfinite(di)) atomicExch(bad, 1);
+            const double wgt = 4.0 * df / S;
+            o[c] = wgt;
+            o[3 + 2 * c] = wgt * dr;
+            o[4 + 2 * c] = wgt * di;
+            acc += wgt * (dr * dr + di * di);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+        ddpart[blockIdx.x] = t;
+    }
+}
+
+int prep_blocks(int N) {
+    const int b = (N + 255) / 256;
+    return b < 4096 ? b : 4096;
+}
+
+cudaError_t launch_prep(const double *d, const double *psd, int N, double df, double *bins,
+                        double *ddpart, int *bad, cudaStream_t s) {
+    prep_kernel<<<prep_blocks(N), 256, 0, s>>>(d, psd, N, df, bins, ddpart, bad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- template
+// Materialise the dense template of walker 0 (injections and element-wise checks):
+// one thread per bin, the same segment rule and evaluation as the fused kernel.
+__device__ __forceinline__ int find_segment(const int *kb, int K, int j) {
+    int lo = 0, hi = K - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (kb[mid] <= j)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) template_kernel(StageDims d, StageBufs b, double *out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d.N) return;
+    const double f = bin_freq(d.f0, d.df, j);
+    double h[6] = {0, 0, 0, 0, 0, 0};
+    if (b.valid[0]) {
+        const double wt = kTwoPi * b.tc[0];
+        for (int mi = 0; mi < d.L; mi++) {
+            const int *bd = b.band + (size_t)mi * 3;
+            if (!bd[0] || j < bd[1] || j > bd[2]) continue;
+            const int s = find_segment(b.kb + (size_t)mi * d.K, d.K, j);
+            const double x = f - b.fk[(size_t)mi * d.K + s];
+            const double *c = b.coef + ((size_t)mi * (d.K - 1) + s) * 32;
+            double v[kNSeries];
+            for (int q = 0; q < kNSeries; q++)
+                v[q] = c[4 * q] + x * (c[4 * q + 1] + x * (c[4 * q + 2] + x * c[4 * q + 3]));
+            double sn, cs;
+            sincos(fma(-wt, f, v[1]), &sn, &cs);
+            const double zr = v[0] * cs, zi = v[0] * sn;
+            for (int ch = 0; ch < 3; ch++) {
+                const double tr = v[2 + 2 * ch], ti = v[3 + 2 * ch];
+                h[2 * ch] += tr * zr - ti * zi;
+                h[2 * ch + 1] += tr * zi + ti * zr;
+            }
+        }
+    }
+    for (int ch = 0; ch < 3; ch++) {
+        out[2 * ((size_t)ch * d.N + j)] = h[2 * ch];
+        out[2 * ((size_t)ch * d.N + j) + 1] = h[2 * ch + 1];
+    }
+}
+
+cudaError_t launch_template(const StageDims &d, const StageBufs &b, double *out, cudaStream_t s) {
+    template_kernel<<<(d.N + 255) / 256, 256, 0, s>>>(d, b, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lisa

@@ -1,0 +1,287 @@
+"""ctypes binding of liblisalike.so (include/lisa_like.h), argument marshalling only.
+
+Function names match the C ABI.  Every step of the likelihood runs in the CUDA
+library; this module converts numpy arrays / torch tensors to pointers and checks
+status codes.  Loading fails loudly when the library is missing: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblisalike.so")
+
+LISA_OK, LISA_ERR_ARG, LISA_ERR_STATE, LISA_ERR_CUDA, LISA_ERR_OOM, LISA_ERR_TIMEOUT = range(6)
+LISA_PREC_FP64, LISA_PREC_SPLIT = 0, 1
+STATUS_NAMES = {0: "LISA_OK", 1: "LISA_ERR_ARG", 2: "LISA_ERR_STATE", 3: "LISA_ERR_CUDA",
+                4: "LISA_ERR_OOM", 5: "LISA_ERR_TIMEOUT"}
+MODES6 = ((2, 2), (3, 3), (4, 4), (2, 1), (3, 2), (4, 3))
+NPAR = 11
+
+# exported symbols (the set the header declares)
+SYMBOLS = (
+    "lisa_like_default_config", "lisa_like_create", "lisa_like_set_data", "lisa_like_loglike",
+    "lisa_like_loglike_device", "lisa_like_data_inner", "lisa_like_template",
+    "lisa_like_stage_knots", "lisa_like_stage_coeffs", "lisa_dl_from_z", "lisa_psd_aet",
+    "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
+    "lisa_like_set_profiling", "lisa_like_read_profile",
+)
+
+
+class lisa_like_config(C.Structure):
+    _fields_ = [
+        ("n_modes", C.c_int),
+        ("modes", (C.c_int * 2) * 6),
+        ("n_knots", C.c_int),
+        ("precision", C.c_int),
+        ("t0_s", C.c_double),
+        ("device", C.c_int),
+        ("stream", C.c_void_p),
+        ("max_batch", C.c_int),
+        ("timeout_s", C.c_double),
+    ]
+
+
+class LisaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblisalike.so (build it first with paper_2005_01827_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("liblisalike.so not found at %s; build it with "
+                          "`python -m paper_2005_01827_gb300.build`" % path)
+    L = C.CDLL(path)
+    vp, dp, i, i64, d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int64, C.c_double
+    cfgp = C.POINTER(lisa_like_config)
+    L.lisa_like_default_config.argtypes = [cfgp]
+    L.lisa_like_default_config.restype = None
+    L.lisa_like_create.argtypes = [cfgp, C.POINTER(vp)]
+    L.lisa_like_create.restype = i
+    L.lisa_like_set_data.argtypes = [vp, d, d, i64, vp, vp]
+    L.lisa_like_set_data.restype = i
+    L.lisa_like_loglike.argtypes = [vp, vp, i, vp, vp, vp]
+    L.lisa_like_loglike.restype = i
+    L.lisa_like_loglike_device.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    L.lisa_like_loglike_device.restype = i
+    L.lisa_like_data_inner.argtypes = [vp, dp]
+    L.lisa_like_data_inner.restype = i
+    L.lisa_like_template.argtypes = [vp, vp, vp]
+    L.lisa_like_template.restype = i
+    L.lisa_like_stage_knots.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    L.lisa_like_stage_knots.restype = i
+    L.lisa_like_stage_coeffs.argtypes = [vp, vp, i, vp]
+    L.lisa_like_stage_coeffs.restype = i
+    L.lisa_dl_from_z.argtypes = [d]
+    L.lisa_dl_from_z.restype = d
+    L.lisa_psd_aet.argtypes = [d, d, i64, vp]
+    L.lisa_psd_aet.restype = i
+    L.lisa_like_set_profiling.argtypes = [vp, i]
+    L.lisa_like_set_profiling.restype = i
+    L.lisa_like_read_profile.argtypes = [vp, dp, C.POINTER(C.c_int)]
+    L.lisa_like_read_profile.restype = i
+    L.lisa_like_last_launches.argtypes = [vp]
+    L.lisa_like_last_launches.restype = i
+    L.lisa_like_destroy.argtypes = [vp]
+    L.lisa_like_destroy.restype = None
+    L.lisa_like_last_error.argtypes = [vp]
+    L.lisa_like_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):            # torch tensor (host or device)
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(st, h=None):
+    if st != LISA_OK:
+        raise LisaError(st, lisa_like_last_error(h))
+
+
+# ------------------------------------------------------------------- C-named wrappers
+
+def lisa_like_default_config() -> lisa_like_config:
+    cfg = lisa_like_config()
+    load().lisa_like_default_config(C.byref(cfg))
+    return cfg
+
+
+def lisa_like_create(cfg: lisa_like_config):
+    h = C.c_void_p()
+    _check(load().lisa_like_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def lisa_like_set_data(h, f0, df, n_bins, d, psd):
+    d = None if d is None else _f64(d)
+    psd = _f64(psd)
+    _check(load().lisa_like_set_data(h, f0, df, n_bins, _ptr(d), _ptr(psd)), h)
+
+
+def lisa_like_loglike(h, params, B, lnL, dh=None, hh=None):
+    _check(load().lisa_like_loglike(h, _ptr(params), B, _ptr(lnL), _ptr(dh), _ptr(hh)), h)
+
+
+def lisa_like_loglike_device(h, d_params, B, d_lnL, d_dh=None, d_hh=None, stream=None):
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(load().lisa_like_loglike_device(h, _ptr(d_params), B, _ptr(d_lnL), _ptr(d_dh),
+                                           _ptr(d_hh), s), h)
+
+
+def lisa_like_data_inner(h) -> float:
+    v = C.c_double()
+    _check(load().lisa_like_data_inner(h, C.byref(v)), h)
+    return v.value
+
+
+def lisa_like_template(h, params, out):
+    _check(load().lisa_like_template(h, _ptr(params), _ptr(out)), h)
+
+
+def lisa_like_stage_knots(h, params, B, band=None, fedge=None, fk=None, vals=None):
+    _check(load().lisa_like_stage_knots(h, _ptr(params), B, _ptr(band), _ptr(fedge), _ptr(fk),
+                                        _ptr(vals)), h)
+
+
+def lisa_like_stage_coeffs(h, params, B, coef):
+    _check(load().lisa_like_stage_coeffs(h, _ptr(params), B, _ptr(coef)), h)
+
+
+def lisa_dl_from_z(z: float) -> float:
+    return load().lisa_dl_from_z(float(z))
+
+
+def lisa_psd_aet(f0, df, n_bins, out):
+    _check(load().lisa_psd_aet(f0, df, n_bins, _ptr(out)))
+
+
+def lisa_like_set_profiling(h, on: bool):
+    _check(load().lisa_like_set_profiling(h, int(bool(on))), h)
+
+
+def lisa_like_read_profile(h):
+    """Per-stage device ms summed since the last read: knots, splines, plan, dense,
+    finish; and the number of calls."""
+    ms = (C.c_double * 5)()
+    n = C.c_int()
+    _check(load().lisa_like_read_profile(h, ms, C.byref(n)), h)
+    return list(ms), n.value
+
+
+def lisa_like_last_launches(h) -> int:
+    return load().lisa_like_last_launches(h)
+
+
+def lisa_like_destroy(h):
+    load().lisa_like_destroy(h)
+
+
+def lisa_like_last_error(h=None) -> str:
+    msg = load().lisa_like_last_error(h)
+    return msg.decode() if msg else ""
+
+
+# ------------------------------------------------------------------- convenience class
+
+class LisaLike:
+    """Owns one handle.  Arrays are numpy (host) unless a method says device."""
+
+    def __init__(self, modes=MODES6, n_knots=1024, precision=LISA_PREC_FP64, t0=3.15576e7,
+                 max_batch=1024, device=0, stream=None, timeout_s=60.0):
+        cfg = lisa_like_default_config()
+        cfg.n_modes = len(modes)
+        for k, (l, m) in enumerate(modes):
+            cfg.modes[k][0], cfg.modes[k][1] = l, m
+        cfg.n_knots, cfg.precision, cfg.t0_s = n_knots, precision, t0
+        cfg.max_batch, cfg.device, cfg.timeout_s = max_batch, device, timeout_s
+        cfg.stream = None if stream is None else int(stream)
+        self.modes, self.K, self.L = tuple(modes), n_knots, len(modes)
+        self.max_batch = max_batch
+        self.h = lisa_like_create(cfg)
+        self.n_bins = 0
+
+    def close(self):
+        if self.h is not None:
+            lisa_like_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, f0, df, n_bins, d, psd):
+        """d complex [3, n_bins] (or None), psd [3, n_bins]."""
+        dd = None
+        if d is not None:
+            d = np.asarray(d)
+            dd = _f64(np.stack([d.real, d.imag], axis=-1)) if np.iscomplexobj(d) else _f64(d)
+        lisa_like_set_data(self.h, f0, df, n_bins, dd, psd)
+        self.n_bins = int(n_bins)
+
+    def loglike(self, params):
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        lnL, dh, hh = np.empty(B), np.empty(B), np.empty(B)
+        lisa_like_loglike(self.h, p, B, lnL, dh, hh)
+        return lnL, dh, hh
+
+    def data_inner(self):
+        return lisa_like_data_inner(self.h)
+
+    def template(self, params):
+        out = np.empty((3, self.n_bins, 2))
+        lisa_like_template(self.h, _f64(params), out)
+        return out[..., 0] + 1j * out[..., 1]
+
+    def stage_knots(self, params):
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        band = np.empty((B, self.L, 3), dtype=np.int64)
+        fedge = np.empty((B, self.L, 2))
+        fk = np.empty((B, self.L, self.K))
+        vals = np.empty((B, self.L, 8, self.K))
+        lisa_like_stage_knots(self.h, p, B, band, fedge, fk, vals)
+        return band, fedge, fk, vals
+
+    def stage_coeffs(self, params):
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        coef = np.empty((B, self.L, self.K - 1, 8, 4))
+        lisa_like_stage_coeffs(self.h, p, B, coef)
+        return coef
+
+    def last_launches(self):
+        return lisa_like_last_launches(self.h)
+
+
+def dl_from_z(z):
+    return np.array([lisa_dl_from_z(v) for v in np.atleast_1d(z)])
+
+
+def psd_aet(f0, df, n_bins):
+    out = np.empty((3, n_bins))
+    lisa_psd_aet(f0, df, n_bins, out)
+    return out
