@@ -269,7 +269,9 @@ def main():
     th = make_inputs(lisalike, like, g, 1 + 1000 * rank, B)
     mode_bins, bins = work_units(like, th)
 
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the kernels and the timing events share it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
     lnL = torch.empty(B, dtype=torch.float64, device="cuda")
     dh = torch.empty_like(lnL)

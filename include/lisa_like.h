@@ -90,9 +90,11 @@ lisa_status lisa_like_set_data(lisa_like_t *h, double f0, double df, int64_t n_b
 lisa_status lisa_like_loglike(lisa_like_t *h, const double *params, int B, double *lnL,
                               double *dh, double *hh);
 
-/* Same on device pointers, asynchronous on `stream` (NULL = the handle's stream).
+/* Same on device pointers, asynchronous on `stream` (a cudaStream_t; NULL is CUDA's
+ * default stream, as everywhere in CUDA).
  *   d_params device double[B][11]; d_lnL device double[B]; d_dh, d_hh device or NULL.
- * The call returns after enqueueing; the caller synchronises the stream. */
+ * The call returns after enqueueing; the caller synchronises the stream.  Calls on one
+ * handle share its work buffers: do not overlap two of them on different streams. */
 lisa_status lisa_like_loglike_device(lisa_like_t *h, const double *d_params, int B,
                                      double *d_lnL, double *d_dh, double *d_hh, void *stream);
 

@@ -419,7 +419,7 @@ lisa_status lisa_like_loglike_device(lisa_like_t *h, const double *d_params, int
     if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
     if (B < 1 || B > h->max_batch) return fail(h, LISA_ERR_ARG, "B must be in [1, max_batch]");
     if (!d_params || !d_lnL) return fail(h, LISA_ERR_ARG, "NULL parameter or output pointer");
-    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    cudaStream_t s = (cudaStream_t)stream;
     LCK(cudaSetDevice(h->device), "cudaSetDevice");
     return run_all(h, d_params, B, d_lnL, d_dh, d_hh, s);
 }
