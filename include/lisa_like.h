@@ -137,6 +137,38 @@ lisa_status lisa_like_set_profiling(lisa_like_t *h, int on);
  * the configured timeout) for those calls, then clears the sums. */
 lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls);
 
+/* Limits of lisa_like_loglike_noalloc and the size of its static scratch. */
+#define LISA_NOALLOC_SCRATCH_BYTES 4194304
+#define LISA_NOALLOC_MAX_WALKER_MODE_KNOTS 8192
+#define LISA_NOALLOC_MAX_ITEMS 16384
+
+/* Batched ln L that allocates no memory (the paper has no counterpart: this entry
+ * exists for callers that cannot call cudaMalloc, e.g. code inside a framework that
+ * owns the whole device heap and gives an operation only its buffers, or a real-time
+ * loop that cannot afford the device synchronisation an allocation implies).  It needs
+ * no handle; the caller passes every input and output as device memory, and all
+ * per-call scratch lives in one static device array of LISA_NOALLOC_SCRATCH_BYTES
+ * inside this library, which every GPU that loads the library holds until exit.
+ *   cfg          n_modes, modes, n_knots and t0_s are used; the other fields ignored.
+ *   f0, df, n_bins  the grid f_j = f0 + j df (as for set_data).
+ *   d_bins       device double[n_bins][9], per bin: w_A, w_E, w_T, then (w d)_A re,
+ *                im, (w d)_E re, im, (w d)_T re, im, with w = 4 df / S_n (Eq. (3)).
+ *   dd           <d|d> of those data (host value; enters ln L only as -dd/2).
+ *   d_params     device double[B][11]; d_lnL device double[B]; d_dh, d_hh device
+ *                double[B] or NULL.
+ *   stream       cudaStream_t (NULL = CUDA's default stream); the call only enqueues.
+ * Limits: B * n_modes * n_knots <= LISA_NOALLOC_MAX_WALKER_MODE_KNOTS and
+ * B * (ceil(n_bins / 1024) + 1) <= LISA_NOALLOC_MAX_ITEMS; larger requests return
+ * LISA_ERR_ARG, and lisa_like_last_error(NULL) on the same thread says which limit.
+ * The first call on a device looks up the scratch address on that device (with it
+ * current), so make that first call before any stream capture.  Every call shares the
+ * one scratch array and leaves its contents behind: calls that overlap on the GPU
+ * (different streams or host threads) race and must be serialised by the caller. */
+lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, double f0, double df,
+                                      int64_t n_bins, const double *d_bins, double dd,
+                                      const double *d_params, int B, double *d_lnL,
+                                      double *d_dh, double *d_hh, void *stream);
+
 /* Number of kernel launches the last loglike / loglike_device call enqueued. */
 int lisa_like_last_launches(const lisa_like_t *h);
 
@@ -144,7 +176,8 @@ int lisa_like_last_launches(const lisa_like_t *h);
 void lisa_like_destroy(lisa_like_t *h);
 
 /* Human-readable description of the last failure on this handle ("" if none);
- * with h == NULL, the last failure of lisa_like_create on this thread. */
+ * with h == NULL, the last failure of lisa_like_create or lisa_like_loglike_noalloc
+ * on this thread. */
 const char *lisa_like_last_error(const lisa_like_t *h);
 
 #ifdef __cplusplus

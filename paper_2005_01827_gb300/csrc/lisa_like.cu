@@ -21,6 +21,11 @@ namespace {
 thread_local std::string g_create_error;
 }
 
+namespace lisa {
+// failure text of handle-free entry points, read back by lisa_like_last_error(NULL)
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace lisa
+
 struct lisa_like {
     int L = 0, K = 0, precision = 0, device = 0, max_batch = 0;
     int ml[6] = {0}, mm[6] = {0};

@@ -28,8 +28,11 @@ SYMBOLS = (
     "lisa_like_loglike_device", "lisa_like_data_inner", "lisa_like_template",
     "lisa_like_stage_knots", "lisa_like_stage_coeffs", "lisa_dl_from_z", "lisa_psd_aet",
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
-    "lisa_like_set_profiling", "lisa_like_read_profile",
+    "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
 )
+NOALLOC_SCRATCH_BYTES = 4194304
+NOALLOC_MAX_WALKER_MODE_KNOTS = 8192
+NOALLOC_MAX_ITEMS = 16384
 
 
 class lisa_like_config(C.Structure):
@@ -92,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.lisa_like_set_profiling.restype = i
     L.lisa_like_read_profile.argtypes = [vp, dp, C.POINTER(C.c_int)]
     L.lisa_like_read_profile.restype = i
+    L.lisa_like_loglike_noalloc.argtypes = [cfgp, d, d, i64, vp, d, vp, i, vp, vp, vp, vp]
+    L.lisa_like_loglike_noalloc.restype = i
     L.lisa_like_last_launches.argtypes = [vp]
     L.lisa_like_last_launches.restype = i
     L.lisa_like_destroy.argtypes = [vp]
@@ -187,6 +192,15 @@ def lisa_like_read_profile(h):
     n = C.c_int()
     _check(load().lisa_like_read_profile(h, ms, C.byref(n)), h)
     return list(ms), n.value
+
+
+def lisa_like_loglike_noalloc(cfg, f0, df, n_bins, d_bins, dd, d_params, B, d_lnL, d_dh=None,
+                              d_hh=None, stream=None):
+    """Allocation-free batched ln L on caller-owned device buffers (see the header)."""
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(load().lisa_like_loglike_noalloc(C.byref(cfg), f0, df, n_bins, _ptr(d_bins), dd,
+                                            _ptr(d_params), B, _ptr(d_lnL), _ptr(d_dh),
+                                            _ptr(d_hh), s))
 
 
 def lisa_like_last_launches(h) -> int:
