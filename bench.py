@@ -58,6 +58,12 @@ def peaks():
     return p
 
 
+def fp32_peak_tflops():
+    """FP32 pipe peak derived from unit counts and clock: 152 SMs x 128 FP32 FMA per
+    clock per SM x 2 flops x 2.07 GHz."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def fp64_peak_tflops():
     """FP64 pipe peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per
     clock per SM x 2 flops x 2.07 GHz (the unit count measured by an FMA-chain probe:
@@ -242,6 +248,49 @@ def run_reference(args, world, rank):
     return 0
 
 
+def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bins):
+    """The same workload in split precision (FP64 knot phases and final sums, FP32
+    in-segment evaluation, sincos, amplitudes, transfers and partial sums)."""
+    import torch
+
+    like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B,
+                    device=torch.cuda.current_device(), precision=lisalike.LISA_PREC_SPLIT)
+    make_inputs(lisalike, like, g, 1, 1)          # same data as the FP64 handle
+    dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
+    lnL = torch.empty(B, dtype=torch.float64, device="cuda")
+
+    def step():
+        lisalike.lisa_like_loglike_device(like.h, dparams, B, lnL, None, None, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    lisalike.lisa_like_set_profiling(like.h, True)
+    lisalike.lisa_like_read_profile(like.h)
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    stage_ms, ncalls = lisalike.lisa_like_read_profile(like.h)
+    like.close()
+    dense_ms = stage_ms[4] / max(ncalls, 1)
+    flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
+    achieved = flops / (dense_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    return {"value": world * B * args.steps / (ms * 1e-3), "unit": "evals/s",
+            "ms_per_step": ms / args.steps, "dtype": "f32+f64",
+            "roofline": {"bound": "alu", "kernel": "dense_split_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
+                         "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
+                                               zip(("knots", "splines", "segprep", "plan",
+                                                    "dense", "finish"), stage_ms)}}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,6 +301,8 @@ def main():
                     help="walkers per GPU (1024 is the benchmark workload; smaller only for "
                          "profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true",
+                    help="skip the split-precision timing of the same workload")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -320,7 +371,7 @@ def main():
     e2e = {"value": world * B * e2e_steps / e2e_s, "unit": "evals/s",
            "h2d_bytes_per_step": B * 11 * 8, "d2h_bytes_per_step": 3 * B * 8}
 
-    dense_ms = stage_ms[3] / max(ncalls, 1)
+    dense_ms = stage_ms[4] / max(ncalls, 1)
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
@@ -329,8 +380,8 @@ def main():
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "units_per_launch": {"walker_mode_bins": mode_bins, "walker_bins": bins},
                 "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
-                                      zip(("knots", "splines", "plan", "dense", "finish"),
-                                          stage_ms)},
+                                      zip(("knots", "splines", "segprep", "plan", "dense",
+                                           "finish"), stage_ms)},
                 "hbm_gbs": BYTES_BIN * bins / (dense_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks().get("hbm_gbs")}
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
@@ -342,9 +393,12 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (data 227 MB, spline coefficients 1.6 GB)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    like.close()
+    if not args.no_split:
+        line["split_precision"] = time_split(lisalike, LisaLike, g, th, B, args, world, stream,
+                                             mode_bins, bins)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and B == 1024:
         line["cpu_baseline"] = cpu_baseline()
-    like.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

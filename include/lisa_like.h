@@ -132,9 +132,10 @@ lisa_status lisa_psd_aet(double f0, double df, int64_t n_bins, double *out);
 lisa_status lisa_like_set_profiling(lisa_like_t *h, int on);
 
 /* Sums of the per-stage device times [ms] of the calls profiled since the last read,
- * ms[0] knots, ms[1] splines, ms[2] work planning, ms[3] fused dense ln L,
- * ms[4] finishing; *n_calls receives the number of calls summed.  Waits (bounded by
- * the configured timeout) for those calls, then clears the sums. */
+ * ms[0] knots, ms[1] splines, ms[2] split-precision segment preparation (0 in FP64),
+ * ms[3] work planning, ms[4] fused dense ln L, ms[5] finishing (ms holds 6 doubles);
+ * *n_calls receives the number of calls summed.  Waits (bounded by the configured
+ * timeout) for those calls, then clears the sums. */
 lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls);
 
 /* Limits of lisa_like_loglike_noalloc and the size of its static scratch. */

@@ -14,6 +14,7 @@
 #include "../../include/lisa_like.h"
 #include "kernels.h"
 #include "model.cuh"
+#include "split.h"
 
 using namespace lisa;
 
@@ -41,7 +42,9 @@ struct lisa_like {
     bool have_data = false;
     double f0 = 0.0, df = 0.0, dd = 0.0;
     int N = 0;
-    double *bins = nullptr;  // [N][9]
+    double *bins = nullptr;   // [N][9] FP64 staged data
+    float *bins32 = nullptr;  // [N][9] FP32 whitened data (split precision)
+    SegRec *segs = nullptr;   // [max_batch][L][K-1] split-precision segment records
 
     // per-call buffers
     double *params = nullptr, *tc = nullptr, *fedge = nullptr, *fk = nullptr, *vals = nullptr;
@@ -53,12 +56,15 @@ struct lisa_like {
     int last_launches = 0;
     std::vector<void *> deferred;  // device buffers that in-flight work may still touch
     bool profiling = false;
-    std::vector<cudaEvent_t> prof_ev;  // 6 events per profiled call
+    std::vector<cudaEvent_t> prof_ev;  // kProfEvents events per profiled call
     int prof_calls = 0;
     std::string err;
 };
 
 namespace {
+
+constexpr int kStages = 6;  // knots, splines, segment prep, plan, dense, finish
+constexpr int kProfEvents = kStages + 1;
 
 lisa_status fail(lisa_like_t *h, lisa_status st, const std::string &msg) {
     if (h) h->err = msg;
@@ -88,6 +94,8 @@ void free_batch(lisa_like_t *h) {
                     h->item_start, h->counter};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->segs) cudaFree(h->segs);
+    h->segs = nullptr;
     h->params = h->tc = h->fedge = h->fk = h->vals = h->mscr = h->coef = h->out = nullptr;
     h->valid = h->band = h->kb = h->wrange = h->item_start = h->counter = nullptr;
     if (h->h_params) cudaFreeHost(h->h_params);
@@ -111,6 +119,8 @@ lisa_status alloc_batch(lisa_like_t *h) {
     LCK(dalloc(&h->item_start, B + 1), "device allocation (items)");
     LCK(dalloc(&h->counter, 1), "device allocation (counter)");
     LCK(dalloc(&h->out, 3 * B), "device allocation (outputs)");
+    if (h->precision == LISA_PREC_SPLIT)
+        LCK(dalloc(&h->segs, B * L * (K - 1)), "device allocation (split segments)");
     LCK(cudaMallocHost(&h->h_params, sizeof(double) * B * kNPar), "pinned allocation");
     LCK(cudaMallocHost(&h->h_out, sizeof(double) * 3 * B), "pinned allocation");
     return LISA_OK;
@@ -179,12 +189,12 @@ lisa_status run_front(lisa_like_t *h, const double *dparams, int B, cudaStream_t
 
 // the events of profiled call `c` (created on first use)
 lisa_status prof_events(lisa_like_t *h, int c, cudaEvent_t **ev) {
-    while ((int)h->prof_ev.size() < 6 * (c + 1)) {
+    while ((int)h->prof_ev.size() < kProfEvents * (c + 1)) {
         cudaEvent_t e;
         LCK(cudaEventCreate(&e), "cudaEventCreate");
         h->prof_ev.push_back(e);
     }
-    *ev = h->prof_ev.data() + 6 * c;
+    *ev = h->prof_ev.data() + kProfEvents * c;
     return LISA_OK;
 }
 
@@ -201,18 +211,27 @@ lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     const StageDims d = dims_of(h, B);
     const StageBufs b = bufs_of(h, dparams);
     const int tile = h->tune.threads * h->tune.per_thread;
+    const bool split = h->precision == LISA_PREC_SPLIT;
     LCK(mark(0), "cudaEventRecord");
     LCK(launch_knots(d, b, s), "knot kernel launch");
     LCK(mark(1), "cudaEventRecord");
     LCK(launch_spline(d, b, s), "spline kernel launch");
     LCK(mark(2), "cudaEventRecord");
-    LCK(launch_plan(d, b, tile, s), "plan kernel launch");
+    if (split) LCK(launch_segprep(d, b, h->segs, s), "segment kernel launch");
     LCK(mark(3), "cudaEventRecord");
-    LCK(launch_dense_f64(d, b, h->bins, h->tune, s), "dense kernel launch");
+    LCK(launch_plan(d, b, tile, s), "plan kernel launch");
     LCK(mark(4), "cudaEventRecord");
-    LCK(launch_finish(d, b, h->dd, lnL, dh, hh, s), "finish kernel launch");
+    if (split)
+        LCK(launch_dense_split(d, b, h->segs, h->bins32, h->tune, s), "dense kernel launch");
+    else
+        LCK(launch_dense_f64(d, b, h->bins, h->tune, s), "dense kernel launch");
     LCK(mark(5), "cudaEventRecord");
-    h->last_launches = 5;
+    if (split)
+        LCK(launch_finish_split(d, b, h->dd, lnL, dh, hh, s), "finish kernel launch");
+    else
+        LCK(launch_finish(d, b, h->dd, lnL, dh, hh, s), "finish kernel launch");
+    LCK(mark(6), "cudaEventRecord");
+    h->last_launches = split ? 6 : 5;
     return LISA_OK;
 }
 
@@ -401,13 +420,34 @@ lisa_status lisa_like_set_data(lisa_like_t *h, double f0, double df, int64_t n_b
     // partial sums of the dense items, sized for the smallest tile any kernel uses
     const int64_t items = max_items(h->max_batch, N, h->min_tile);
     double *part = nullptr;
-    if ((e = dalloc(&part, (size_t)items * 2)) != cudaSuccess) {
+    float *bins32 = nullptr;
+    if ((e = dalloc(&part, (size_t)items * 2)) != cudaSuccess ||
+        (h->precision == LISA_PREC_SPLIT &&
+         (e = dalloc(&bins32, (size_t)kBinFloats * N)) != cudaSuccess)) {
+        if (part) cudaFree(part);
         cudaFree(bins);
-        return cuda_fail(h, e, "device allocation (partial sums)");
+        return cuda_fail(h, e, "device allocation (partial sums / FP32 data)");
+    }
+    if (bins32) {
+        if ((e = launch_prep_split(bins, N, bins32, s)) != cudaSuccess) {
+            cudaFree(part);
+            cudaFree(bins32);
+            cudaFree(bins);
+            return cuda_fail(h, e, "FP32 data preparation");
+        }
+        st = wait_for(h, s);
+        if (st != LISA_OK) {
+            h->deferred.push_back(part);
+            h->deferred.push_back(bins32);
+            h->deferred.push_back(bins);
+            return st;
+        }
     }
     if (h->bins) cudaFree(h->bins);
+    if (h->bins32) cudaFree(h->bins32);
     if (h->part) cudaFree(h->part);
     h->bins = bins;
+    h->bins32 = bins32;
     h->part = part;
     h->part_items = items;
     h->f0 = f0;
@@ -537,14 +577,14 @@ lisa_status lisa_like_set_profiling(lisa_like_t *h, int on) {
 
 lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls) {
     if (!h || !ms) return LISA_ERR_ARG;
-    for (int i = 0; i < 5; i++) ms[i] = 0.0;
+    for (int i = 0; i < kStages; i++) ms[i] = 0.0;
     const int n = h->prof_calls;
     if (n_calls) *n_calls = n;
     if (n == 0) return LISA_OK;
     LCK(cudaSetDevice(h->device), "cudaSetDevice");
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        const cudaError_t e = cudaEventQuery(h->prof_ev[6 * (n - 1) + 5]);
+        const cudaError_t e = cudaEventQuery(h->prof_ev[kProfEvents * (n - 1) + kStages]);
         if (e == cudaSuccess) break;
         if (e != cudaErrorNotReady) return cuda_fail(h, e, "device work failed");
         if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
@@ -553,9 +593,10 @@ lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls) {
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     for (int c = 0; c < n; c++)
-        for (int i = 0; i < 5; i++) {
+        for (int i = 0; i < kStages; i++) {
             float t = 0.0f;
-            LCK(cudaEventElapsedTime(&t, h->prof_ev[6 * c + i], h->prof_ev[6 * c + i + 1]),
+            LCK(cudaEventElapsedTime(&t, h->prof_ev[kProfEvents * c + i],
+                                     h->prof_ev[kProfEvents * c + i + 1]),
                 "cudaEventElapsedTime");
             ms[i] += t;
         }
@@ -578,6 +619,7 @@ void lisa_like_destroy(lisa_like_t *h) {
             cudaFree(p);
     }
     if (h->bins) cudaFree(h->bins);
+    if (h->bins32) cudaFree(h->bins32);
     if (h->part) cudaFree(h->part);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     if (h->done) cudaEventDestroy(h->done);

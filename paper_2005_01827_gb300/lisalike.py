@@ -186,9 +186,9 @@ def lisa_like_set_profiling(h, on: bool):
 
 
 def lisa_like_read_profile(h):
-    """Per-stage device ms summed since the last read: knots, splines, plan, dense,
-    finish; and the number of calls."""
-    ms = (C.c_double * 5)()
+    """Per-stage device ms summed since the last read: knots, splines, segment prep,
+    plan, dense, finish; and the number of calls."""
+    ms = (C.c_double * 6)()
     n = C.c_int()
     _check(load().lisa_like_read_profile(h, ms, C.byref(n)), h)
     return list(ms), n.value
