@@ -153,7 +153,8 @@ lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls);
  *   cfg          n_modes, modes, n_knots and t0_s are used; the other fields ignored.
  *   f0, df, n_bins  the grid f_j = f0 + j df (as for set_data).
  *   d_bins       device double[n_bins][9], per bin: w_A, w_E, w_T, then (w d)_A re,
- *                im, (w d)_E re, im, (w d)_T re, im, with w = 4 df / S_n (Eq. (3)).
+ *                im, (w d)_E re, im, (w d)_T re, im, with w = 4 df / S_n (Eq. (3));
+ *                16-byte aligned (as cudaMalloc and torch allocations are).
  *   dd           <d|d> of those data (host value; enters ln L only as -dd/2).
  *   d_params     device double[B][11]; d_lnL device double[B]; d_dh, d_hh device
  *                double[B] or NULL.

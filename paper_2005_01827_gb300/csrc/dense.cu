@@ -1,13 +1,15 @@
-// dense.cu -- the fused dense kernel of the batched LISA likelihood (Katz et al. 2020,
-// Sec. II.A): spline interpolation of A, phase and T onto the dense bins, the mode
+// dense.cu -- the fused FP64 dense kernel of the batched LISA likelihood (Katz et al.
+// 2020, Sec. II.A): spline interpolation of A, phase and T onto the dense bins, the mode
 // sum, and the noise-weighted inner products of Eqs. (3) and (11), reduced to one
-// <d|h>, <h|h> pair per work item.  The dense template is never stored.
+// (<d|h>, <h|h>) pair per (work item, walker).  The dense template is never stored.
 //
-// Work item = (walker, tile of consecutive bins inside the union of the walker's
-// active mode ranges).  Blocks are persistent and pull items from a counter, so
-// walkers with very different bands (masses spanning decades) load-balance.
+// Work item = (walker group, tile of consecutive bins inside the group's union band).
+// One bulk copy (TMA) stages the tile's w and w d (72 bytes per bin) in shared memory;
+// every walker of the group then reads them from there.  Blocks are persistent and pull
+// items from a counter.
 #include "kernels.h"
 #include "model.cuh"
+#include "tma.cuh"
 
 namespace lisa {
 
@@ -39,128 +41,181 @@ __device__ __forceinline__ void eval_segment(const double *__restrict__ c, doubl
     }
 }
 
-template <int C>
+// group of a work item: largest g with item_start[g] <= item
+__device__ __forceinline__ int group_of(const int *__restrict__ item_start, int ng, int item) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int C, int G>
 __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b,
                                                         const double *__restrict__ bins,
                                                         int tile_bins) {
-    __shared__ int s_item;
+    extern __shared__ __align__(128) unsigned char smem[];
+    double *sbin = reinterpret_cast<double *>(smem);  // [tile_bins][9]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + sizeof(double) * kBinDoubles * tile_bins);
+    __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
+    __shared__ double s_tc[G];
     __shared__ double red[2][4];
-    const int total = b.item_start[d.B];
+    const int tid = threadIdx.x;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    const int ng = n_groups(d.B, G);
+    const int total = b.item_start[ng];
     const int K = d.K;
+    uint32_t parity = 0;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
+        if (tid == 0) s_item = atomicAdd(b.counter, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-
-        int lo = 0, hi = d.B - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (b.item_start[mid] <= item)
-                lo = mid;
-            else
-                hi = mid - 1;
+        const int g = group_of(b.item_start, ng, item);
+        const int J0 = b.grange[2 * g] + (item - b.item_start[g]) * tile_bins;
+        const int Jend = min(J0 + tile_bins, b.grange[2 * g + 1] + 1);
+        // whole groups of 4 rows (16-byte multiples) by one bulk copy, the last <= 3 rows
+        // by plain loads, so nothing past the end of the data is read
+        const int full = (Jend - J0) & ~3, tail = Jend - J0 - full;
+        if (tid == 0 && full > 0) {
+            fence_proxy_async();
+            tma_load_1d(sbin, bins + (size_t)J0 * kBinDoubles,
+                        (uint32_t)(full * kBinDoubles * sizeof(double)), bar);
         }
-        const int w = lo;
-        const int J0 = b.wrange[2 * w] + (item - b.item_start[w]) * tile_bins;
-        const int Jend = min(J0 + tile_bins, b.wrange[2 * w + 1] + 1);
-        const int j0 = J0 + (int)threadIdx.x * C;
-        const double wtc = kTwoPi * b.tc[w];
-
-        int seg[kMaxModes], jlo[kMaxModes], jhi[kMaxModes];
-#pragma unroll
-        for (int mi = 0; mi < kMaxModes; mi++) {
-            jlo[mi] = 1;
-            jhi[mi] = 0;
-            seg[mi] = 0;
-            if (mi < d.L) {
+        if (tid < tail * kBinDoubles)
+            sbin[full * kBinDoubles + tid] = bins[((size_t)J0 + full) * kBinDoubles + tid];
+        if (tid < G) {
+            const int i = g * G + tid;
+            const int w = i < d.B ? b.order[i] : -1;
+            s_walker[tid] = w;
+            s_tc[tid] = w >= 0 ? kTwoPi * b.tc[w] : 0.0;
+        }
+        if (tid < G * kMaxModes) {
+            const int k = tid / kMaxModes, mi = tid % kMaxModes;
+            const int i = g * G + k;
+            int lo = 1, hi = 0;
+            if (i < d.B && mi < d.L) {
+                const int w = b.order[i];
                 const int *bd = b.band + ((size_t)w * d.L + mi) * 3;
-                if (bd[0]) {
-                    jlo[mi] = bd[1];
-                    jhi[mi] = bd[2];
+                if (b.valid[w] && bd[0]) {
+                    lo = bd[1];
+                    hi = bd[2];
                 }
-                const int jj = max(j0, jlo[mi]);
-                if (jj <= jhi[mi] && jj < min(j0 + C, Jend))
-                    seg[mi] = segment_of(b.kb + ((size_t)w * d.L + mi) * K, K, jj);
             }
-        }
-
-        double dh = 0.0, hh = 0.0;
-        for (int i = 0; i < C; i++) {
-            const int j = j0 + i;
-            if (j >= Jend) break;
-            const double f = bin_freq_d(d.f0, d.df, j);
-            double hr0 = 0.0, hi0 = 0.0, hr1 = 0.0, hi1 = 0.0, hr2 = 0.0, hi2 = 0.0;
-#pragma unroll
-            for (int mi = 0; mi < kMaxModes; mi++) {
-                if (mi >= d.L || j < jlo[mi] || j > jhi[mi]) continue;
-                const size_t wm = (size_t)w * d.L + mi;
-                const int *kbm = b.kb + wm * K;
-                int s = seg[mi];
-                while (s < K - 2 && j >= __ldg(kbm + s + 1)) s++;
-                seg[mi] = s;
-                const double x = f - __ldg(b.fk + wm * K + s);
-                double v[kNSeries];
-                eval_segment(b.coef + (wm * (K - 1) + s) * 32, x, v);
-                double sn, cs;
-                sincos(fma(-wtc, f, v[1]), &sn, &cs);
-                const double zr = v[0] * cs, zi = v[0] * sn;
-                hr0 = fma(v[2], zr, fma(-v[3], zi, hr0));
-                hi0 = fma(v[2], zi, fma(v[3], zr, hi0));
-                hr1 = fma(v[4], zr, fma(-v[5], zi, hr1));
-                hi1 = fma(v[4], zi, fma(v[5], zr, hi1));
-                hr2 = fma(v[6], zr, fma(-v[7], zi, hr2));
-                hi2 = fma(v[6], zi, fma(v[7], zr, hi2));
-            }
-            const double *o = bins + (size_t)j * kBinDoubles;
-            hh = fma(__ldg(o + 0), fma(hr0, hr0, hi0 * hi0), hh);
-            hh = fma(__ldg(o + 1), fma(hr1, hr1, hi1 * hi1), hh);
-            hh = fma(__ldg(o + 2), fma(hr2, hr2, hi2 * hi2), hh);
-            dh = fma(__ldg(o + 3), hr0, fma(__ldg(o + 4), hi0, dh));
-            dh = fma(__ldg(o + 5), hr1, fma(__ldg(o + 6), hi1, dh));
-            dh = fma(__ldg(o + 7), hr2, fma(__ldg(o + 8), hi2, dh));
-        }
-
-        for (int o = 16; o > 0; o >>= 1) {
-            dh += __shfl_down_sync(0xffffffffu, dh, o);
-            hh += __shfl_down_sync(0xffffffffu, hh, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            red[0][threadIdx.x >> 5] = dh;
-            red[1][threadIdx.x >> 5] = hh;
+            s_lo[k][mi] = lo;
+            s_hi[k][mi] = hi;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, c = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
-                a += red[0][k];
-                c += red[1][k];
+        if (full > 0) {
+            // every thread waits; the block leaves together if the copy never completed
+            if (!__syncthreads_and(mbar_wait_bounded(bar, parity, b.err))) return;
+            parity ^= 1u;
+        }
+
+        for (int k = 0; k < G; k++) {
+            const int w = s_walker[k];
+            if (w < 0) continue;
+            const size_t slot = (size_t)item * G + k;
+            if (b.wrange[2 * w + 1] < J0 || b.wrange[2 * w] >= Jend) {
+                if (tid == 0) {
+                    b.part[2 * slot] = 0.0;
+                    b.part[2 * slot + 1] = 0.0;
+                }
+                continue;
             }
-            b.part[2 * (size_t)item] = a;
-            b.part[2 * (size_t)item + 1] = c;
+            const int j0 = J0 + tid * C;
+            const double wtc = s_tc[k];
+            int seg[kMaxModes];
+#pragma unroll
+            for (int mi = 0; mi < kMaxModes; mi++) {
+                seg[mi] = 0;
+                const int jj = max(j0, s_lo[k][mi]);
+                if (mi < d.L && jj <= s_hi[k][mi] && jj < min(j0 + C, Jend))
+                    seg[mi] = segment_of(b.kb + ((size_t)w * d.L + mi) * K, K, jj);
+            }
+            double dh = 0.0, hh = 0.0;
+            for (int i = 0; i < C; i++) {
+                const int j = j0 + i;
+                if (j >= Jend) break;
+                const double f = bin_freq_d(d.f0, d.df, j);
+                double hr0 = 0.0, hi0 = 0.0, hr1 = 0.0, hi1 = 0.0, hr2 = 0.0, hi2 = 0.0;
+#pragma unroll
+                for (int mi = 0; mi < kMaxModes; mi++) {
+                    if (mi >= d.L || j < s_lo[k][mi] || j > s_hi[k][mi]) continue;
+                    const size_t wm = (size_t)w * d.L + mi;
+                    const int *kbm = b.kb + wm * K;
+                    int s = seg[mi];
+                    while (s < K - 2 && j >= __ldg(kbm + s + 1)) s++;
+                    seg[mi] = s;
+                    const double x = f - __ldg(b.fk + wm * K + s);
+                    double v[kNSeries];
+                    eval_segment(b.coef + (wm * (K - 1) + s) * 32, x, v);
+                    double sn, cs;
+                    sincos(fma(-wtc, f, v[1]), &sn, &cs);
+                    const double zr = v[0] * cs, zi = v[0] * sn;
+                    hr0 = fma(v[2], zr, fma(-v[3], zi, hr0));
+                    hi0 = fma(v[2], zi, fma(v[3], zr, hi0));
+                    hr1 = fma(v[4], zr, fma(-v[5], zi, hr1));
+                    hi1 = fma(v[4], zi, fma(v[5], zr, hi1));
+                    hr2 = fma(v[6], zr, fma(-v[7], zi, hr2));
+                    hi2 = fma(v[6], zi, fma(v[7], zr, hi2));
+                }
+                const double *o = sbin + (size_t)(j - J0) * kBinDoubles;
+                hh = fma(o[0], fma(hr0, hr0, hi0 * hi0), hh);
+                hh = fma(o[1], fma(hr1, hr1, hi1 * hi1), hh);
+                hh = fma(o[2], fma(hr2, hr2, hi2 * hi2), hh);
+                dh = fma(o[3], hr0, fma(o[4], hi0, dh));
+                dh = fma(o[5], hr1, fma(o[6], hi1, dh));
+                dh = fma(o[7], hr2, fma(o[8], hi2, dh));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dh += __shfl_down_sync(0xffffffffu, dh, o);
+                hh += __shfl_down_sync(0xffffffffu, hh, o);
+            }
+            if ((tid & 31) == 0) {
+                red[0][tid >> 5] = dh;
+                red[1][tid >> 5] = hh;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0.0, c = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+                    a += red[0][q];
+                    c += red[1][q];
+                }
+                b.part[2 * slot] = a;
+                b.part[2 * slot + 1] = c;
+            }
+            __syncthreads();
         }
     }
+}
+
+template <int C, int G>
+cudaError_t launch_f64(const StageDims &d, const StageBufs &b, const double *bins, int blocks,
+                       cudaStream_t s) {
+    const int tile = 128 * C;
+    const size_t smem = sizeof(double) * kBinDoubles * tile + 16;
+    cudaError_t e = cudaFuncSetAttribute(dense_f64_kernel<C, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dense_f64_kernel<C, G><<<blocks, 128, smem, s>>>(d, b, bins, tile);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
                              const DenseTune &t, cudaStream_t s) {
     if (t.threads != 128) return cudaErrorInvalidValue;
-    const int tile = t.threads * t.per_thread;
-    switch (t.per_thread) {
-        case 4:
-            dense_f64_kernel<4><<<t.blocks, 128, 0, s>>>(d, b, bins, tile);
-            break;
-        case 8:
-            dense_f64_kernel<8><<<t.blocks, 128, 0, s>>>(d, b, bins, tile);
-            break;
-        case 16:
-            dense_f64_kernel<16><<<t.blocks, 128, 0, s>>>(d, b, bins, tile);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (t.per_thread == 8 && t.group == 8) return launch_f64<8, 8>(d, b, bins, t.blocks, s);
+    if (t.per_thread == 8 && t.group == 1) return launch_f64<8, 1>(d, b, bins, t.blocks, s);
+    if (t.per_thread == 4 && t.group == 8) return launch_f64<4, 8>(d, b, bins, t.blocks, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lisa

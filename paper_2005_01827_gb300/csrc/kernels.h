@@ -31,32 +31,44 @@ struct StageBufs {
     double *vals;          // [B][L][8][K]
     double *mscratch;      // [B][L][8][K] second derivatives of the spline
     double *coef;          // [B][L][K-1][8][4]
-    int *wrange;           // [B][2] union of the active mode ranges
-    int *item_start;       // [B+1] exclusive prefix of the dense work items
+    int *wrange;           // [B][2] union of the walker's active mode ranges
+    int *order;            // [B] walkers sorted by band (groups are runs of G entries)
+    int *slot_of;          // [B] position of each walker in `order`
+    int *grange;           // [groups][2] union range of each group (start a multiple of 4)
+    int *item_start;       // [groups+1] exclusive prefix of the dense work items
     int *counter;          // dense work-queue counter
-    double *part;          // [items][2] per-item <d|h>, <h|h>
+    int *err;              // set by a device wait that gave up
+    double *part;          // [items][G][2] per-item, per-slot partial sums
 };
 
 struct DenseTune {
     int threads;     // threads per block
     int per_thread;  // consecutive bins per thread
     int blocks;      // persistent grid size
+    int group;       // walkers sharing one staged data tile
 };
+
+// groups of a call with B walkers
+__host__ __device__ inline int n_groups(int B, int G) { return (B + G - 1) / G; }
 
 cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
-cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, cudaStream_t s);
+cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, int group,
+                        cudaStream_t s);
 cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
                              const DenseTune &t, cudaStream_t s);
-cudaError_t launch_finish(const StageDims &d, const StageBufs &b, double dd, double *lnL,
-                          double *dh, double *hh, cudaStream_t s);
+// split = 0: parts hold (<d|h>, <h|h>); split = 1: (sum |h|^2 - 2 Re(d h*), <h|h>)
+cudaError_t launch_finish(const StageDims &d, const StageBufs &b, int group, int split, double dd,
+                          double *lnL, double *dh, double *hh, cudaStream_t s);
 cudaError_t launch_template(const StageDims &d, const StageBufs &b, double *out,
                             cudaStream_t s);
 cudaError_t launch_prep(const double *d, const double *psd, int N, double df, double *bins,
                         double *ddpart, int *bad, cudaStream_t s);
 int prep_blocks(int N);
 
-// Largest number of dense work items a call with B walkers can produce.
+// Largest number of (item, slot) partial-sum pairs a call with B walkers can produce.
 int64_t max_items(int B, int N, int tile_bins);
+// Bytes of dynamic shared memory the planning kernel needs for B walkers.
+size_t plan_smem(int B);
 
 }  // namespace lisa

@@ -35,7 +35,7 @@ struct lisa_like {
     bool own_stream = false;
     cudaEvent_t done = nullptr;
     int n_sm = 0;
-    DenseTune tune = {128, 8, 0};
+    DenseTune tune = {128, 8, 0, 8};
     int min_tile = 512;  // smallest tile the dense kernels use (sizes the partial sums)
 
     // data
@@ -50,9 +50,11 @@ struct lisa_like {
     double *params = nullptr, *tc = nullptr, *fedge = nullptr, *fk = nullptr, *vals = nullptr;
     double *mscr = nullptr, *coef = nullptr, *part = nullptr, *out = nullptr;
     int *valid = nullptr, *band = nullptr, *kb = nullptr, *wrange = nullptr;
-    int *item_start = nullptr, *counter = nullptr;
+    int *order = nullptr, *slot_of = nullptr, *grange = nullptr;
+    int *item_start = nullptr, *counter = nullptr, *err_flag = nullptr;
     int64_t part_items = 0;
     double *h_params = nullptr, *h_out = nullptr;  // pinned staging
+    int *h_err = nullptr;
     int last_launches = 0;
     std::vector<void *> deferred;  // device buffers that in-flight work may still touch
     bool profiling = false;
@@ -89,18 +91,21 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_batch(lisa_like_t *h) {
-    void *ptrs[] = {h->params, h->tc,   h->fedge,  h->fk,     h->vals,       h->mscr,
-                    h->coef,   h->out,  h->valid,  h->band,   h->kb,         h->wrange,
-                    h->item_start, h->counter};
+    void *ptrs[] = {h->params, h->tc,    h->fedge,  h->fk,     h->vals,       h->mscr,
+                    h->coef,   h->out,   h->valid,  h->band,   h->kb,         h->wrange,
+                    h->order,  h->slot_of, h->grange, h->item_start, h->counter, h->err_flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    h->order = h->slot_of = h->grange = h->err_flag = nullptr;
     if (h->segs) cudaFree(h->segs);
     h->segs = nullptr;
     h->params = h->tc = h->fedge = h->fk = h->vals = h->mscr = h->coef = h->out = nullptr;
     h->valid = h->band = h->kb = h->wrange = h->item_start = h->counter = nullptr;
     if (h->h_params) cudaFreeHost(h->h_params);
     if (h->h_out) cudaFreeHost(h->h_out);
+    if (h->h_err) cudaFreeHost(h->h_err);
     h->h_params = h->h_out = nullptr;
+    h->h_err = nullptr;
 }
 
 lisa_status alloc_batch(lisa_like_t *h) {
@@ -116,13 +121,19 @@ lisa_status alloc_batch(lisa_like_t *h) {
     LCK(dalloc(&h->mscr, B * L * kNSeries * K), "device allocation (spline scratch)");
     LCK(dalloc(&h->coef, B * L * (K - 1) * 32), "device allocation (spline coefficients)");
     LCK(dalloc(&h->wrange, 2 * B), "device allocation (ranges)");
+    LCK(dalloc(&h->order, B), "device allocation (order)");
+    LCK(dalloc(&h->slot_of, B), "device allocation (slots)");
+    LCK(dalloc(&h->grange, 2 * B), "device allocation (group ranges)");
     LCK(dalloc(&h->item_start, B + 1), "device allocation (items)");
     LCK(dalloc(&h->counter, 1), "device allocation (counter)");
+    LCK(dalloc(&h->err_flag, 1), "device allocation (error flag)");
+    LCK(cudaMemset(h->err_flag, 0, sizeof(int)), "cudaMemset");
     LCK(dalloc(&h->out, 3 * B), "device allocation (outputs)");
     if (h->precision == LISA_PREC_SPLIT)
         LCK(dalloc(&h->segs, B * L * (K - 1)), "device allocation (split segments)");
     LCK(cudaMallocHost(&h->h_params, sizeof(double) * B * kNPar), "pinned allocation");
     LCK(cudaMallocHost(&h->h_out, sizeof(double) * 3 * B), "pinned allocation");
+    LCK(cudaMallocHost(&h->h_err, sizeof(int)), "pinned allocation");
     return LISA_OK;
 }
 
@@ -139,8 +150,12 @@ StageBufs bufs_of(const lisa_like_t *h, const double *params) {
     b.mscratch = h->mscr;
     b.coef = h->coef;
     b.wrange = h->wrange;
+    b.order = h->order;
+    b.slot_of = h->slot_of;
+    b.grange = h->grange;
     b.item_start = h->item_start;
     b.counter = h->counter;
+    b.err = h->err_flag;
     b.part = h->part;
     return b;
 }
@@ -219,17 +234,15 @@ lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     LCK(mark(2), "cudaEventRecord");
     if (split) LCK(launch_segprep(d, b, h->segs, s), "segment kernel launch");
     LCK(mark(3), "cudaEventRecord");
-    LCK(launch_plan(d, b, tile, s), "plan kernel launch");
+    LCK(launch_plan(d, b, tile, h->tune.group, s), "plan kernel launch");
     LCK(mark(4), "cudaEventRecord");
     if (split)
         LCK(launch_dense_split(d, b, h->segs, h->bins32, h->tune, s), "dense kernel launch");
     else
         LCK(launch_dense_f64(d, b, h->bins, h->tune, s), "dense kernel launch");
     LCK(mark(5), "cudaEventRecord");
-    if (split)
-        LCK(launch_finish_split(d, b, h->dd, lnL, dh, hh, s), "finish kernel launch");
-    else
-        LCK(launch_finish(d, b, h->dd, lnL, dh, hh, s), "finish kernel launch");
+    LCK(launch_finish(d, b, h->tune.group, split ? 1 : 0, h->dd, lnL, dh, hh, s),
+        "finish kernel launch");
     LCK(mark(6), "cudaEventRecord");
     h->last_launches = split ? 6 : 5;
     return LISA_OK;
@@ -484,8 +497,12 @@ lisa_status lisa_like_loglike(lisa_like_t *h, const double *params, int B, doubl
     if (st != LISA_OK) return st;
     LCK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s),
         "result download");
+    LCK(cudaMemcpyAsync(h->h_err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s),
+        "result download");
     st = wait_for(h, s);
     if (st != LISA_OK) return st;
+    if (*h->h_err)
+        return fail(h, LISA_ERR_TIMEOUT, "a device wait for staged data gave up (outputs are NaN)");
     std::memcpy(lnL, h->h_out, sizeof(double) * B);
     if (dh) std::memcpy(dh, h->h_out + B, sizeof(double) * B);
     if (hh) std::memcpy(hh, h->h_out + 2 * B, sizeof(double) * B);

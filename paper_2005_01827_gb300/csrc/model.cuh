@@ -290,7 +290,8 @@ __device__ inline void make_frame(const Source &s, Frame &fr) {
         }
 }
 
-// constellation centre p0 and spacecraft offsets q[i] (seconds) at time t
+// constellation centre p0 and spacecraft offsets q[i] (seconds) at time t; the angles
+// 2 alpha - b_i and alpha - b_i come from one sincos of alpha by angle addition
 __device__ inline void constellation(double t, double p0[3], double q[3][3]) {
     const double R = kAuM / kClight, L = kArmM / kClight;
     const double al = kTwoPi * t / kYearS;
@@ -299,15 +300,17 @@ __device__ inline void constellation(double t, double p0[3], double q[3][3]) {
     p0[0] = R * ca;
     p0[1] = R * sa;
     p0[2] = 0.0;
+    const double s2a = 2.0 * sa * ca, c2a = ca * ca - sa * sa;
     const double pre = L / (4.0 * sqrt(3.0));
+    const double cb[3] = {1.0, -0.5, -0.5};
+    const double sbv[3] = {0.0, 0.8660254037844386, -0.8660254037844386};
+#pragma unroll
     for (int i = 0; i < 3; i++) {
-        const double b = kTwoPi * i / 3.0;
-        double s1, c1, s2, c2, cb, sbb;
-        sincos(2.0 * al - b, &s1, &c1);
-        sincos(al - b, &s2, &c2);
-        sincos(b, &sbb, &cb);
-        q[i][0] = pre * (c1 - 3.0 * cb);
-        q[i][1] = pre * (s1 - 3.0 * sbb);
+        const double c1 = c2a * cb[i] + s2a * sbv[i];  // cos(2 al - b)
+        const double s1 = s2a * cb[i] - c2a * sbv[i];  // sin(2 al - b)
+        const double c2 = ca * cb[i] + sa * sbv[i];    // cos(al - b)
+        q[i][0] = pre * (c1 - 3.0 * cb[i]);
+        q[i][1] = pre * (s1 - 3.0 * sbv[i]);
         q[i][2] = -2.0 * sqrt(3.0) * pre * c2;
     }
 }
@@ -319,7 +322,9 @@ __device__ inline double delay_phase(const Frame &fr, double f, double t) {
     return -kTwoPi * f * (fr.k[0] * p0[0] + fr.k[1] * p0[1] + fr.k[2] * p0[2]);
 }
 
-// TDI A, E, T transfer of one mode at (f, t), Eqs. (7)-(10)
+// TDI A, E, T transfer of one mode at (f, t), Eqs. (7)-(10).  The two directions of an
+// arm share n n^T (so the polarisation factor) and the propagation phase; only the
+// sinc argument differs.
 __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f, double t,
                                     cplx out[3], double *delay) {
     double p0[3], q[3][3];
@@ -328,42 +333,45 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
     const double L = kArmM / kClight;
     const double pfl = kPi * f * L;
     cplx y[3][3];  // y[emitter][receiver]
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
 #pragma unroll
-    for (int sidx = 0; sidx < 3; sidx++)
+    for (int e = 0; e < 3; e++) {
+        const int a = pa[e], c = pb[e];
+        double n[3];
+        double nn = 0.0;
 #pragma unroll
-        for (int r = 0; r < 3; r++) {
-            if (sidx == r) {
-                y[sidx][r] = {0.0, 0.0};
-                continue;
-            }
-            double n[3];
-            double nn = 0.0;
-            for (int a = 0; a < 3; a++) {
-                n[a] = q[r][a] - q[sidx][a];
-                nn += n[a] * n[a];
-            }
-            const double inv = 1.0 / sqrt(nn);
-            for (int a = 0; a < 3; a++) n[a] *= inv;
-            double kn = 0.0, kq = 0.0, xp = 0.0, xc = 0.0;
-            for (int a = 0; a < 3; a++) {
-                kn += fr.k[a] * n[a];
-                kq += fr.k[a] * (q[sidx][a] + q[r][a]);
-                double tp = 0.0, tcx = 0.0;
-                for (int b = 0; b < 3; b++) {
-                    tp += fr.ep[a][b] * n[b];
-                    tcx += fr.ec[a][b] * n[b];
-                }
-                xp += n[a] * tp;
-                xc += n[a] * tcx;
-            }
-            const double arg = pfl * (1.0 - kn);
-            const double sinc = (arg == 0.0) ? 1.0 : sin(arg) / arg;
-            const cplx F = {kp.re * xp + kc.re * xc, kp.im * xp + kc.im * xc};
-            const cplx e = cexpi(-kPi * f * (L + kq));
-            // -i pfl sinc e F
-            const cplx eF = cmul(e, F);
-            y[sidx][r] = {pfl * sinc * eF.im, -pfl * sinc * eF.re};
+        for (int i = 0; i < 3; i++) {
+            n[i] = q[c][i] - q[a][i];
+            nn += n[i] * n[i];
         }
+        const double inv = 1.0 / sqrt(nn);
+        double kn = 0.0, kq = 0.0, xp = 0.0, xc = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            n[i] *= inv;
+            kn += fr.k[i] * n[i];
+            kq += fr.k[i] * (q[a][i] + q[c][i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            double tp = 0.0, tcx = 0.0;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                tp += fr.ep[i][j] * n[j];
+                tcx += fr.ec[i][j] * n[j];
+            }
+            xp += n[i] * tp;
+            xc += n[i] * tcx;
+        }
+        const cplx F = {kp.re * xp + kc.re * xc, kp.im * xp + kc.im * xc};
+        const cplx eF = cmul(cexpi(-kPi * f * (L + kq)), F);
+        const double a1 = pfl * (1.0 - kn), a2 = pfl * (1.0 + kn);  // a -> c and c -> a
+        const double s1 = (a1 == 0.0) ? 1.0 : sin(a1) / a1;
+        const double s2 = (a2 == 0.0) ? 1.0 : sin(a2) / a2;
+        // -i pfl sinc e F
+        y[a][c] = {pfl * s1 * eF.im, -pfl * s1 * eF.re};
+        y[c][a] = {pfl * s2 * eF.im, -pfl * s2 * eF.re};
+    }
     const cplx D = cexpi(-kTwoPi * f * L);
     const cplx D2 = cmul(D, D);
     const cplx fac = {1.0 - D2.re, -D2.im};

@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -37,7 +38,8 @@ void *g_addr[kMaxDevices] = {nullptr};
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t valid, tc, band, fedge, fk, kb, vals, mscr, coef, wrange, items, counter, part, end;
+    size_t valid, tc, band, fedge, fk, kb, vals, mscr, coef, wrange, order, slot, grange, items,
+        counter, err, part, end;
 };
 
 Layout layout_for(size_t B, size_t L, size_t K, size_t items) {
@@ -58,8 +60,12 @@ Layout layout_for(size_t B, size_t L, size_t K, size_t items) {
     o.mscr = take(sizeof(double) * B * L * kNSeries * K);
     o.coef = take(sizeof(double) * B * L * (K - 1) * 32);
     o.wrange = take(sizeof(int) * 2 * B);
+    o.order = take(sizeof(int) * B);
+    o.slot = take(sizeof(int) * B);
+    o.grange = take(sizeof(int) * 2 * B);
     o.items = take(sizeof(int) * (B + 1));
     o.counter = take(sizeof(int));
+    o.err = take(sizeof(int));
     o.part = take(sizeof(double) * 2 * items);
     o.end = p;
     return o;
@@ -116,8 +122,10 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
         return arg_error("grid needs finite f0 > 0, df > 0; t0 and <d|d> must be finite");
     if (n_bins < 1 || n_bins >= ((int64_t)1 << 31)) return arg_error("n_bins must be in [1, 2^31)");
     if (B < 1) return arg_error("B must be >= 1");
+    if (((uintptr_t)d_bins & 15) != 0) return arg_error("d_bins must be 16-byte aligned");
     const int64_t blk = (int64_t)B * L * K;
-    const int64_t items = max_items(B, (int)n_bins, kTile);
+    // one walker per group here: (item, walker) pairs = B x tiles of at most n_bins + 3 bins
+    const int64_t items = (int64_t)B * ((n_bins + 3 + kTile - 1) / kTile + 1);
     if (blk > LISA_NOALLOC_MAX_WALKER_MODE_KNOTS)
         return arg_error("B * n_modes * n_knots exceeds the no-alloc limit (8192)");
     if (items > LISA_NOALLOC_MAX_ITEMS)
@@ -146,8 +154,12 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
     b.mscratch = reinterpret_cast<double *>(s8 + o.mscr);
     b.coef = reinterpret_cast<double *>(s8 + o.coef);
     b.wrange = reinterpret_cast<int *>(s8 + o.wrange);
+    b.order = reinterpret_cast<int *>(s8 + o.order);
+    b.slot_of = reinterpret_cast<int *>(s8 + o.slot);
+    b.grange = reinterpret_cast<int *>(s8 + o.grange);
     b.item_start = reinterpret_cast<int *>(s8 + o.items);
     b.counter = reinterpret_cast<int *>(s8 + o.counter);
+    b.err = reinterpret_cast<int *>(s8 + o.err);
     b.part = reinterpret_cast<double *>(s8 + o.part);
 
     StageDims d;
@@ -162,16 +174,18 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
         d.ml[i] = i < L ? cfg->modes[i][0] : 0;
         d.mm[i] = i < L ? cfg->modes[i][1] : 0;
     }
-    const DenseTune tune = {128, 8, nsm * 4};
+    const DenseTune tune = {128, 8, nsm * 2, 1};
     cudaStream_t s = (cudaStream_t)stream;
-    // Every buffer is written before it is read within the call; the work counter, the
-    // only value that must start at zero, is cleared by the planning kernel.
+    // Every buffer is written before it is read within the call; the work counter and the
+    // error flag, the only values that must start at zero, are cleared by the planning
+    // kernel.
     if ((e = launch_knots(d, b, s)) != cudaSuccess) return cuda_error(e, "knot kernel launch");
     if ((e = launch_spline(d, b, s)) != cudaSuccess) return cuda_error(e, "spline kernel launch");
-    if ((e = launch_plan(d, b, kTile, s)) != cudaSuccess) return cuda_error(e, "plan kernel launch");
+    if ((e = launch_plan(d, b, kTile, tune.group, s)) != cudaSuccess)
+        return cuda_error(e, "plan kernel launch");
     if ((e = launch_dense_f64(d, b, d_bins, tune, s)) != cudaSuccess)
         return cuda_error(e, "dense kernel launch");
-    if ((e = launch_finish(d, b, dd, d_lnL, d_dh, d_hh, s)) != cudaSuccess)
+    if ((e = launch_finish(d, b, tune.group, 0, dd, d_lnL, d_dh, d_hh, s)) != cudaSuccess)
         return cuda_error(e, "finish kernel launch");
     return LISA_OK;
 }

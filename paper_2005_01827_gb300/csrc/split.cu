@@ -12,6 +12,7 @@
 #include "kernels.h"
 #include "model.cuh"
 #include "split.h"
+#include "tma.cuh"
 
 namespace lisa {
 
@@ -128,16 +129,15 @@ cudaError_t launch_segprep(const StageDims &d, const StageBufs &b, SegRec *segs,
 }
 
 // ------------------------------------------------------------------------ dense
-__device__ __forceinline__ int seg_of(const int *__restrict__ kb, int K, int j) {
-    int lo = 0, hi = K - 2;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(kb + mid) <= j)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
+// segment of bin j from the log spacing of the knots (MUFU log2 guess), then moved by
+// the integer knot-to-bin boundaries so that kb[s] <= j < kb[s + 1]
+__device__ __forceinline__ int seg_guess(const int *__restrict__ kb, int K, int j, float fjf,
+                                         float flo, float scale) {
+    int s = (int)(__log2f(__fdividef(fjf, flo)) * scale);
+    s = min(max(s, 0), K - 2);
+    while (s > 0 && __ldg(kb + s) > j) s--;
+    while (s < K - 2 && __ldg(kb + s + 1) <= j) s++;
+    return s;
 }
 
 struct PhaseState {
@@ -149,8 +149,10 @@ struct PhaseState {
 __device__ __forceinline__ PhaseState phase_at(const SegRec &r, int n) {
     const long long nn = n;
     const unsigned long long c1 = (unsigned long long)nn;
-    const unsigned long long c2 = (unsigned long long)(nn * (nn - 1) / 2);
-    const unsigned long long c3 = (unsigned long long)(nn * (nn - 1) * (nn - 2) / 6);
+    // n(n-1) >= 0 and even; n(n-1)(n-2)/2 is a multiple of 3, so multiplying by the
+    // inverse of 3 modulo 2^64 divides it exactly
+    const unsigned long long c2 = (unsigned long long)(nn * (nn - 1)) >> 1;
+    const unsigned long long c3 = (c2 * (unsigned long long)(nn - 2)) * 0xAAAAAAAAAAAAAAABull;
     PhaseState p;
     p.ph = r.p[0] + c1 * r.p[1] + c2 * r.p[2] + c3 * r.p[3];
     p.d1 = r.p[1] + c1 * r.p[2] + c2 * r.p[3];
@@ -174,185 +176,277 @@ __device__ __forceinline__ void phasor(unsigned long long ph, const float2 *__re
     zi = fmaf(t.x, sn, t.y * cs);
 }
 
-template <int C>
+__device__ __forceinline__ int group_of_s(const int *__restrict__ item_start, int ng, int item) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// error-free sum of two floats: a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// warp sum of FP32 (value, compensation) pairs, kept as an unevaluated hi + lo pair
+__device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+}
+
+template <int C, int G>
 __global__ void __launch_bounds__(128) dense_split_kernel(StageDims d, StageBufs b,
                                                           const SegRec *__restrict__ segs,
                                                           const float *__restrict__ bins,
                                                           int tile_bins) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sbin = reinterpret_cast<float *>(smem);  // [tile_bins][9]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + sizeof(float) * kBinFloats * tile_bins);
     __shared__ float2 tab[256];
-    __shared__ int s_item;
+    __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
+    __shared__ float s_flo[G][kMaxModes], s_scl[G][kMaxModes];
     __shared__ double red[2][4];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int k = tid; k < 256; k += blockDim.x) {
         double sn, cs;
         sincospi((double)k / 128.0, &sn, &cs);
         tab[k] = make_float2((float)cs, (float)sn);
     }
-    const int total = b.item_start[d.B];
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    const int ng = n_groups(d.B, G);
+    const int total = b.item_start[ng];
     const int K = d.K;
+    const float f0f = (float)d.f0, dff = (float)d.df;
+    uint32_t parity = 0;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
+        if (tid == 0) s_item = atomicAdd(b.counter, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        int lo = 0, hi = d.B - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (b.item_start[mid] <= item)
-                lo = mid;
-            else
-                hi = mid - 1;
+        const int g = group_of_s(b.item_start, ng, item);
+        const int J0 = b.grange[2 * g] + (item - b.item_start[g]) * tile_bins;
+        const int Jend = min(J0 + tile_bins, b.grange[2 * g + 1] + 1);
+        // whole groups of 4 rows (16-byte multiples) by one bulk copy, the last <= 3 rows
+        // by plain loads, so nothing past the end of the data is read
+        const int full = (Jend - J0) & ~3, tail = Jend - J0 - full;
+        if (tid == 0 && full > 0) {
+            fence_proxy_async();
+            tma_load_1d(sbin, bins + (size_t)J0 * kBinFloats,
+                        (uint32_t)(full * kBinFloats * sizeof(float)), bar);
         }
-        const int w = lo;
-        const int J0 = b.wrange[2 * w] + (item - b.item_start[w]) * tile_bins;
-        const int Jend = min(J0 + tile_bins, b.wrange[2 * w + 1] + 1);
-        const int j0 = J0 + (int)threadIdx.x * C;
+        if (tid < tail * kBinFloats)
+            sbin[full * kBinFloats + tid] = bins[((size_t)J0 + full) * kBinFloats + tid];
+        if (tid < G) {
+            const int i = g * G + tid;
+            s_walker[tid] = i < d.B ? b.order[i] : -1;
+        }
+        if (tid < G * kMaxModes) {
+            const int k = tid / kMaxModes, mi = tid % kMaxModes;
+            const int i = g * G + k;
+            int lo = 1, hi = 0;
+            float flo = 1.0f, scl = 0.0f;
+            if (i < d.B && mi < d.L) {
+                const int w = b.order[i];
+                const size_t wm = (size_t)w * d.L + mi;
+                const int *bd = b.band + wm * 3;
+                if (b.valid[w] && bd[0]) {
+                    lo = bd[1];
+                    hi = bd[2];
+                    const double f_lo = b.fedge[2 * wm], f_hi = b.fedge[2 * wm + 1];
+                    flo = (float)f_lo;
+                    scl = (float)((double)(K - 1) / log2(f_hi / f_lo));
+                }
+            }
+            s_lo[k][mi] = lo;
+            s_hi[k][mi] = hi;
+            s_flo[k][mi] = flo;
+            s_scl[k][mi] = scl;
+        }
+        __syncthreads();
+        if (full > 0) {
+            // every thread waits; the block leaves together if the copy never completed
+            if (!__syncthreads_and(mbar_wait_bounded(bar, parity, b.err))) return;
+            parity ^= 1u;
+        }
 
-        float hr[C][3], hm[C][3];
+        for (int k = 0; k < G; k++) {
+            const int w = s_walker[k];
+            if (w < 0) continue;
+            const size_t slot = (size_t)item * G + k;
+            if (b.wrange[2 * w + 1] < J0 || b.wrange[2 * w] >= Jend) {
+                if (tid == 0) {
+                    b.part[2 * slot] = 0.0;
+                    b.part[2 * slot + 1] = 0.0;
+                }
+                continue;
+            }
+            const int j0 = J0 + tid * C;
+            float hr[C][3], hm[C][3];
 #pragma unroll
-        for (int i = 0; i < C; i++)
+            for (int i = 0; i < C; i++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                hr[i][c] = 0.0f;
-                hm[i][c] = 0.0f;
+                for (int c = 0; c < 3; c++) {
+                    hr[i][c] = 0.0f;
+                    hm[i][c] = 0.0f;
+                }
+            for (int mi = 0; mi < d.L; mi++) {
+                const int ja = max(j0, s_lo[k][mi]);
+                const int jb = min(min(j0 + C, Jend), s_hi[k][mi] + 1);
+                if (ja >= jb) continue;
+                const size_t wm = (size_t)w * d.L + mi;
+                const int *kb = b.kb + wm * K;
+                const SegRec *sg = segs + wm * (K - 1);
+                int s = seg_guess(kb, K, ja, fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
+                SegRec r = sg[s];
+                int knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
+                PhaseState p = phase_at(r, ja - r.kb0);
+                float t = (float)(ja - r.kb0) * r.invw;
+                if (ja == j0 && jb == j0 + C && knext >= j0 + C) {
+                    // the whole chunk lies in one segment and in the band: no predicates
+#pragma unroll
+                    for (int i = 0; i < C; i++) {
+                        float v[7];
+#pragma unroll
+                        for (int q = 0; q < 7; q++)
+                            v[q] = fmaf(t, fmaf(t, fmaf(t, r.c[4 * q + 3], r.c[4 * q + 2]),
+                                                r.c[4 * q + 1]),
+                                        r.c[4 * q]);
+                        float zr, zi;
+                        phasor(p.ph, tab, zr, zi);
+                        zr *= v[0];
+                        zi *= v[0];
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            const float tr = v[1 + 2 * c], ti = v[2 + 2 * c];
+                            hr[i][c] = fmaf(tr, zr, fmaf(-ti, zi, hr[i][c]));
+                            hm[i][c] = fmaf(tr, zi, fmaf(ti, zr, hm[i][c]));
+                        }
+                        p.ph += p.d1;
+                        p.d1 += p.d2;
+                        p.d2 += p.d3;
+                        t += r.invw;
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int i = 0; i < C; i++) {
+                    const int j = j0 + i;
+                    if (j < ja || j >= jb) continue;
+                    if (j >= knext) {  // the chunk crosses into the next segment
+                        s++;
+                        r = sg[s];
+                        knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
+                        p = phase_at(r, j - r.kb0);
+                        t = (float)(j - r.kb0) * r.invw;
+                    }
+                    float v[7];
+#pragma unroll
+                    for (int q = 0; q < 7; q++)
+                        v[q] = fmaf(t, fmaf(t, fmaf(t, r.c[4 * q + 3], r.c[4 * q + 2]),
+                                            r.c[4 * q + 1]),
+                                    r.c[4 * q]);
+                    float zr, zi;
+                    phasor(p.ph, tab, zr, zi);
+                    zr *= v[0];
+                    zi *= v[0];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float tr = v[1 + 2 * c], ti = v[2 + 2 * c];
+                        hr[i][c] = fmaf(tr, zr, fmaf(-ti, zi, hr[i][c]));
+                        hm[i][c] = fmaf(tr, zi, fmaf(ti, zr, hm[i][c]));
+                    }
+                    p.ph += p.d1;
+                    p.d1 += p.d2;
+                    p.d2 += p.d3;
+                    t += r.invw;
+                }
             }
 
-        for (int mi = 0; mi < d.L; mi++) {
-            const size_t wm = (size_t)w * d.L + mi;
-            const int *bd = b.band + wm * 3;
-            if (!bd[0]) continue;
-            const int ja = max(j0, bd[1]);
-            const int jb = min(min(j0 + C, Jend), bd[2] + 1);
-            if (ja >= jb) continue;
-            const int *kb = b.kb + wm * K;
-            const SegRec *sg = segs + wm * (K - 1);
-            int s = seg_of(kb, K, ja);
-            SegRec r = sg[s];
-            int knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
-            PhaseState p = phase_at(r, ja - r.kb0);
-            float t = (float)(ja - r.kb0) * r.invw;
+            // per-bin integrand |h|^2 - 2 Re(d h*) and |h|^2 in whitened units, compensated
+            float rs = 0.0f, rc = 0.0f, hs = 0.0f, hc = 0.0f;
 #pragma unroll
             for (int i = 0; i < C; i++) {
                 const int j = j0 + i;
-                if (j < ja || j >= jb) continue;
-                if (j >= knext) {  // the chunk crosses into the next segment
-                    s++;
-                    r = sg[s];
-                    knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
-                    p = phase_at(r, j - r.kb0);
-                    t = (float)(j - r.kb0) * r.invw;
-                }
-                float v[7];
-#pragma unroll
-                for (int q = 0; q < 7; q++)
-                    v[q] = fmaf(t, fmaf(t, fmaf(t, r.c[4 * q + 3], r.c[4 * q + 2]), r.c[4 * q + 1]),
-                                r.c[4 * q]);
-                float zr, zi;
-                phasor(p.ph, tab, zr, zi);
-                zr *= v[0];
-                zi *= v[0];
+                if (j >= Jend) continue;
+                const float *o = sbin + (j - J0) * kBinFloats;
+                float ri = 0.0f, hi2 = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const float tr = v[1 + 2 * c], ti = v[2 + 2 * c];
-                    hr[i][c] = fmaf(tr, zr, fmaf(-ti, zi, hr[i][c]));
-                    hm[i][c] = fmaf(tr, zi, fmaf(ti, zr, hm[i][c]));
+                    const float sw = o[c];
+                    const float xr = sw * hr[i][c], xi = sw * hm[i][c];
+                    const float er = fmaf(-2.0f, o[3 + 2 * c], xr);
+                    const float ei = fmaf(-2.0f, o[4 + 2 * c], xi);
+                    ri = fmaf(xr, er, fmaf(xi, ei, ri));
+                    hi2 = fmaf(xr, xr, fmaf(xi, xi, hi2));
                 }
-                p.ph += p.d1;
-                p.d1 += p.d2;
-                p.d2 += p.d3;
-                t += r.invw;
+                float y = ri - rc;
+                float tt = rs + y;
+                rc = (tt - rs) - y;
+                rs = tt;
+                y = hi2 - hc;
+                tt = hs + y;
+                hc = (tt - hs) - y;
+                hs = tt;
             }
-        }
-
-        // per-bin integrand |h|^2 - 2 Re(d h*) and |h|^2 in whitened units, compensated
-        float rs = 0.0f, rc = 0.0f, hs = 0.0f, hc = 0.0f;
-#pragma unroll
-        for (int i = 0; i < C; i++) {
-            const int j = j0 + i;
-            if (j >= Jend) continue;
-            const float *o = bins + (size_t)j * kBinFloats;
-            float ri = 0.0f, hi2 = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float sw = __ldg(o + c);
-                const float xr = sw * hr[i][c], xi = sw * hm[i][c];
-                const float er = fmaf(-2.0f, __ldg(o + 3 + 2 * c), xr);
-                const float ei = fmaf(-2.0f, __ldg(o + 4 + 2 * c), xi);
-                ri = fmaf(xr, er, fmaf(xi, ei, ri));
-                hi2 = fmaf(xr, xr, fmaf(xi, xi, hi2));
+            // FP32 (value, compensation) pairs summed across the warp; FP64 from here up
+            float rl = -rc, hl = -hc;
+            warp_sum_pair(rs, rl);
+            warp_sum_pair(hs, hl);
+            if ((tid & 31) == 0) {
+                red[0][tid >> 5] = (double)rs + (double)rl;
+                red[1][tid >> 5] = (double)hs + (double)hl;
             }
-            // Kahan-Babuska compensated accumulation
-            float y = ri - rc;
-            float tt = rs + y;
-            rc = (tt - rs) - y;
-            rs = tt;
-            y = hi2 - hc;
-            tt = hs + y;
-            hc = (tt - hs) - y;
-            hs = tt;
-        }
-        double R = (double)rs - (double)rc, H = (double)hs - (double)hc;
-        for (int o = 16; o > 0; o >>= 1) {
-            R += __shfl_down_sync(0xffffffffu, R, o);
-            H += __shfl_down_sync(0xffffffffu, H, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            red[0][threadIdx.x >> 5] = R;
-            red[1][threadIdx.x >> 5] = H;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, c = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
-                a += red[0][k];
-                c += red[1][k];
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0.0, c = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+                    a += red[0][q];
+                    c += red[1][q];
+                }
+                b.part[2 * slot] = a;
+                b.part[2 * slot + 1] = c;
             }
-            b.part[2 * (size_t)item] = a;
-            b.part[2 * (size_t)item + 1] = c;
+            __syncthreads();
         }
     }
+}
+
+template <int C, int G>
+cudaError_t launch_split(const StageDims &d, const StageBufs &b, const SegRec *segs,
+                         const float *bins, int blocks, cudaStream_t s) {
+    const int tile = 128 * C;
+    const size_t smem = sizeof(float) * kBinFloats * tile + 16;
+    cudaError_t e = cudaFuncSetAttribute(dense_split_kernel<C, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dense_split_kernel<C, G><<<blocks, 128, smem, s>>>(d, b, segs, bins, tile);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_split(const StageDims &d, const StageBufs &b, const SegRec *segs,
                                const float *bins, const DenseTune &t, cudaStream_t s) {
     if (t.threads != 128) return cudaErrorInvalidValue;
-    const int tile = t.threads * t.per_thread;
-    switch (t.per_thread) {
-        case 8:
-            dense_split_kernel<8><<<t.blocks, 128, 0, s>>>(d, b, segs, bins, tile);
-            break;
-        case 16:
-            dense_split_kernel<16><<<t.blocks, 128, 0, s>>>(d, b, segs, bins, tile);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-// ln L = -(sum of |h|^2 - 2 Re(d h*))/2 - <d|d>/2; <h|h> and <d|h> follow from the sums
-__global__ void finish_split_kernel(StageDims d, StageBufs b, double dd, double *lnL, double *dh,
-                                    double *hh) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= d.B) return;
-    double R = 0.0, H = 0.0;
-    if (b.valid[w]) {
-        for (int i = b.item_start[w]; i < b.item_start[w + 1]; i++) {
-            R += b.part[2 * (size_t)i];
-            H += b.part[2 * (size_t)i + 1];
-        }
-        lnL[w] = -0.5 * R - 0.5 * dd;
-    } else {
-        lnL[w] = -INFINITY;
-    }
-    if (dh) dh[w] = 0.5 * (H - R);
-    if (hh) hh[w] = H;
-}
-
-cudaError_t launch_finish_split(const StageDims &d, const StageBufs &b, double dd, double *lnL,
-                                double *dh, double *hh, cudaStream_t s) {
-    finish_split_kernel<<<(d.B + 127) / 128, 128, 0, s>>>(d, b, dd, lnL, dh, hh);
-    return cudaGetLastError();
+    if (t.per_thread == 8 && t.group == 8) return launch_split<8, 8>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 8 && t.group == 1) return launch_split<8, 1>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 16 && t.group == 8)
+        return launch_split<16, 8>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 4 && t.group == 8) return launch_split<4, 8>(d, b, segs, bins, t.blocks, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lisa

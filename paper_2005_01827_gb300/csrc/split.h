@@ -28,7 +28,5 @@ cudaError_t launch_prep_split(const double *bins, int N, float *out, cudaStream_
 cudaError_t launch_segprep(const StageDims &d, const StageBufs &b, SegRec *segs, cudaStream_t s);
 cudaError_t launch_dense_split(const StageDims &d, const StageBufs &b, const SegRec *segs,
                                const float *bins, const DenseTune &t, cudaStream_t s);
-cudaError_t launch_finish_split(const StageDims &d, const StageBufs &b, double dd, double *lnL,
-                                double *dh, double *hh, cudaStream_t s);
 
 }  // namespace lisa

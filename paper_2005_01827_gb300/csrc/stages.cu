@@ -131,15 +131,19 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
     if (!b.band[(size_t)wm * 3]) return;
     const int K = d.K, n = K;
     double *hh = sh;            // [K-1] knot spacings
-    double *den = sh + K;       // [K] Thomas pivots
-    double *cpr = sh + 2 * K;   // [K] normalised super-diagonal
-    double *sub = sh + 3 * K;   // [K] sub-diagonal
+    double *ih = sh + K;        // [K-1] their reciprocals
+    double *dinv = sh + 2 * K;  // [K] reciprocal Thomas pivots
+    double *cpr = sh + 3 * K;   // [K] normalised super-diagonal
+    double *sub = sh + 4 * K;   // [K] sub-diagonal
     const double *x = b.fk + (size_t)wm * K;
     const double *y = b.vals + (size_t)wm * kNSeries * K;
     double *Mv = b.mscratch + (size_t)wm * kNSeries * K;
     const int lane = threadIdx.x;
 
-    for (int k = lane; k < n - 1; k += 32) hh[k] = x[k + 1] - x[k];
+    for (int k = lane; k < n - 1; k += 32) {
+        hh[k] = x[k + 1] - x[k];
+        ih[k] = 1.0 / hh[k];
+    }
     __syncwarp();
     if (lane == 0) {
         for (int i = 1; i <= n - 2; i++) {
@@ -147,16 +151,17 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
             double sup = hh[i];
             double sb = hh[i - 1];
             if (i == 1) {
-                dia += hh[0] * (hh[0] + hh[1]) / hh[1];
-                sup -= hh[0] * hh[0] / hh[1];
+                dia += hh[0] * (hh[0] + hh[1]) * ih[1];
+                sup -= hh[0] * hh[0] * ih[1];
             }
             if (i == n - 2) {
-                dia += hh[n - 2] * (hh[n - 3] + hh[n - 2]) / hh[n - 3];
-                sb -= hh[n - 2] * hh[n - 2] / hh[n - 3];
+                dia += hh[n - 2] * (hh[n - 3] + hh[n - 2]) * ih[n - 3];
+                sb -= hh[n - 2] * hh[n - 2] * ih[n - 3];
             }
             const double pv = (i == 1) ? dia : dia - sb * cpr[i - 1];
-            den[i] = pv;
-            cpr[i] = sup / pv;
+            const double inv = 1.0 / pv;
+            dinv[i] = inv;
+            cpr[i] = sup * inv;
             sub[i] = sb;
         }
     }
@@ -165,12 +170,12 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
         const double *yq = y + (size_t)lane * K;
         double *Mq = Mv + (size_t)lane * K;
         double prev = 0.0;
-        double dprev = (yq[1] - yq[0]) / hh[0];
+        double dprev = (yq[1] - yq[0]) * ih[0];
         for (int i = 1; i <= n - 2; i++) {
-            const double dcur = (yq[i + 1] - yq[i]) / hh[i];
+            const double dcur = (yq[i + 1] - yq[i]) * ih[i];
             const double rhs = 6.0 * (dcur - dprev);
             dprev = dcur;
-            const double rp = (i == 1) ? rhs / den[1] : (rhs - sub[i] * prev) / den[i];
+            const double rp = (rhs - sub[i] * prev) * dinv[i];
             Mq[i] = rp;
             prev = rp;
         }
@@ -179,8 +184,8 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
             nxt = Mq[i] - cpr[i] * nxt;
             Mq[i] = nxt;
         }
-        Mq[0] = ((hh[0] + hh[1]) * Mq[1] - hh[0] * Mq[2]) / hh[1];
-        Mq[n - 1] = ((hh[n - 3] + hh[n - 2]) * Mq[n - 2] - hh[n - 2] * Mq[n - 3]) / hh[n - 3];
+        Mq[0] = ((hh[0] + hh[1]) * Mq[1] - hh[0] * Mq[2]) * ih[1];
+        Mq[n - 1] = ((hh[n - 3] + hh[n - 2]) * Mq[n - 2] - hh[n - 2] * Mq[n - 3]) * ih[n - 3];
     }
     __syncwarp();
     double *cm = b.coef + (size_t)wm * (K - 1) * 32;
@@ -188,18 +193,18 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
         const int sgm = t / kNSeries, q = t % kNSeries;
         const double *yq = y + (size_t)q * K;
         const double *Mq = Mv + (size_t)q * K;
-        const double h = hh[sgm];
+        const double h = hh[sgm], hi = ih[sgm];
         const double m0 = Mq[sgm], m1 = Mq[sgm + 1];
         double *c = cm + (size_t)sgm * 32 + q * 4;
         c[0] = yq[sgm];
-        c[1] = (yq[sgm + 1] - yq[sgm]) / h - h * (2.0 * m0 + m1) / 6.0;
+        c[1] = (yq[sgm + 1] - yq[sgm]) * hi - h * (2.0 * m0 + m1) * (1.0 / 6.0);
         c[2] = 0.5 * m0;
-        c[3] = (m1 - m0) / (6.0 * h);
+        c[3] = (m1 - m0) * hi * (1.0 / 6.0);
     }
 }
 
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
-    const size_t smem = sizeof(double) * 4 * (size_t)d.K;
+    const size_t smem = sizeof(double) * 5 * (size_t)d.K;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(spline_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -207,103 +212,6 @@ cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s
         if (e != cudaSuccess) return e;
     }
     spline_kernel<<<d.B * d.L, 32, smem, s>>>(d, b);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------- planning
-// Union of each walker's active mode ranges, split into tiles of tile_bins bins; the
-// exclusive prefix over walkers numbers the dense work items.  One block; also resets
-// the work-queue counter so the whole call needs no host round trip.
-__global__ void __launch_bounds__(1024) plan_kernel(StageDims d, StageBufs b, int tile_bins) {
-    __shared__ int warp_tot[32];
-    __shared__ int carry;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        carry = 0;
-        *b.counter = 0;
-    }
-    __syncthreads();
-    for (int base = 0; base < d.B; base += blockDim.x) {
-        const int w = base + tid;
-        int cnt = 0;
-        if (w < d.B) {
-            int lo = 0x7fffffff, hi = -1;
-            for (int mi = 0; mi < d.L; mi++) {
-                const int *bd = b.band + ((size_t)w * d.L + mi) * 3;
-                if (bd[0] && b.valid[w]) {
-                    lo = min(lo, bd[1]);
-                    hi = max(hi, bd[2]);
-                }
-            }
-            if (hi < lo) {
-                lo = 0;
-                hi = -1;
-            }
-            b.wrange[2 * w] = lo;
-            b.wrange[2 * w + 1] = hi;
-            cnt = hi >= lo ? (hi - lo + tile_bins) / tile_bins : 0;
-        }
-        // block-wide exclusive scan of cnt
-        int v = cnt;
-        const int lane = tid & 31, wid = tid >> 5;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane == 31) warp_tot[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            int t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += u;
-            }
-            warp_tot[lane] = t;
-        }
-        __syncthreads();
-        const int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + v - cnt;
-        if (w < d.B) b.item_start[w] = excl;
-        __syncthreads();
-        if (tid == blockDim.x - 1) carry = excl + cnt;
-        __syncthreads();
-    }
-    if (tid == 0) b.item_start[d.B] = carry;
-}
-
-cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, cudaStream_t s) {
-    plan_kernel<<<1, 1024, 0, s>>>(d, b, tile_bins);
-    return cudaGetLastError();
-}
-
-int64_t max_items(int B, int N, int tile_bins) {
-    return (int64_t)B * (((int64_t)N + tile_bins - 1) / tile_bins + 1);
-}
-
-// ---------------------------------------------------------------------------- finish
-// ln L = <d|h> - <h|h>/2 - <d|d>/2 (Eq. (2)); per-walker sums of the dense items are
-// taken in item order, so results do not depend on which block ran which item.
-__global__ void finish_kernel(StageDims d, StageBufs b, double dd, double *lnL, double *dh,
-                              double *hh) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= d.B) return;
-    double a = 0.0, c = 0.0;
-    if (b.valid[w]) {
-        const int i0 = b.item_start[w], i1 = b.item_start[w + 1];
-        for (int i = i0; i < i1; i++) {
-            a += b.part[2 * (size_t)i];
-            c += b.part[2 * (size_t)i + 1];
-        }
-        lnL[w] = a - 0.5 * c - 0.5 * dd;
-    } else {
-        lnL[w] = -INFINITY;
-    }
-    if (dh) dh[w] = a;
-    if (hh) hh[w] = c;
-}
-
-cudaError_t launch_finish(const StageDims &d, const StageBufs &b, double dd, double *lnL,
-                          double *dh, double *hh, cudaStream_t s) {
-    finish_kernel<<<(d.B + 127) / 128, 128, 0, s>>>(d, b, dd, lnL, dh, hh);
     return cudaGetLastError();
 }
 
