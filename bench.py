@@ -36,6 +36,9 @@ METRIC = "ln L evals/s (6 modes, A/E/T, 1-yr df)"
 WORKLOAD = ("1024 walkers, 6 modes (2,2),(3,3),(4,4),(2,1),(3,2),(4,3), K=1024 knots, "
             "1-yr grid 1e-5..1e-1 Hz at df=1/3.15576e7 s (3155445 bins), A/E/T, FP64, "
             "Binary-1 injection + seeded noise")
+WORKLOAD_C3 = ("8192 walkers with M_T log-uniform in [1e3, 1e9] Msun, 6 modes, K=1024 knots, "
+               "1-yr grid (3155445 bins), A/E/T, FP64, CUDA-graph replay, autotuned tiles, "
+               "Binary-1 injection + seeded noise")
 # algorithmic FP64 work (see the design notes): per (walker, mode, active bin) 8 cubic
 # Horner evaluations (48), the segment offset (1), the t_coal ramp (2), A e^{i phi} (2),
 # three complex transfer products (18), the mode sum (6) = 77 flops plus one sincos
@@ -154,7 +157,7 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
-def make_inputs(lisalike, like, g, seed_walkers, B):
+def make_inputs(lisalike, like, g, seed_walkers, B, logm=(5.0, 7.0)):
     """Data (Binary-1 injection by the library + noise of Eq. (12)) and walkers."""
     psd = np.empty((3, g.n_bins))
     lisalike.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
@@ -165,7 +168,7 @@ def make_inputs(lisalike, like, g, seed_walkers, B):
     sig = 0.5 * np.sqrt(psd / g.df)
     d = h + sig * (z[..., 0] + 1j * z[..., 1])
     like.set_data(g.f0, g.df, g.n_bins, d, psd)
-    th = W.draw_walkers(B, seed_walkers, (5.0, 7.0))
+    th = W.draw_walkers(B, seed_walkers, logm)
     th[:, 4] = [lisalike.lisa_dl_from_z(v) for v in th[:, 4]]
     return th
 
@@ -248,7 +251,7 @@ def run_reference(args, world, rank):
     return 0
 
 
-def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bins):
+def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bins, graphs=False):
     """The same workload in split precision (FP64 knot phases and final sums, FP32
     in-segment evaluation, sincos, amplitudes, transfers and partial sums)."""
     import torch
@@ -256,6 +259,8 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B,
                     device=torch.cuda.current_device(), precision=lisalike.LISA_PREC_SPLIT)
     make_inputs(lisalike, like, g, 1, 1)          # same data as the FP64 handle
+    if graphs:
+        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
     dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
     lnL = torch.empty(B, dtype=torch.float64, device="cuda")
 
@@ -265,8 +270,11 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
-    lisalike.lisa_like_set_profiling(like.h, True)
-    lisalike.lisa_like_read_profile(like.h)
+    stage_ms, ncalls = profile_once(lisalike, like, step)
+    if graphs:
+        lisalike.lisa_like_set_graphs(like.h, True)
+        step()
+    torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -275,20 +283,31 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(world, e0.elapsed_time(e1))
-    stage_ms, ncalls = lisalike.lisa_like_read_profile(like.h)
+    shape = lisalike.lisa_like_get_tune(like.h)
     like.close()
     dense_ms = stage_ms[4] / max(ncalls, 1)
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     return {"value": world * B * args.steps / (ms * 1e-3), "unit": "evals/s",
-            "ms_per_step": ms / args.steps, "dtype": "f32+f64",
+            "ms_per_step": ms / args.steps, "dtype": "f32+f64", "graphs": graphs,
+            "tile": {"bins_per_thread": shape[0], "group": shape[1], "blocks": shape[2]},
             "roofline": {"bound": "alu", "kernel": "dense_split_kernel", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
                          "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
                                                zip(("knots", "splines", "segprep", "plan",
                                                     "dense", "finish"), stage_ms)}}}
+
+
+def profile_once(lisalike, like, step):
+    """Per-stage CUDA-event times of one call (profiling off afterwards)."""
+    lisalike.lisa_like_set_profiling(like.h, True)
+    lisalike.lisa_like_read_profile(like.h)
+    step()
+    stage_ms, n = lisalike.lisa_like_read_profile(like.h)
+    lisalike.lisa_like_set_profiling(like.h, False)
+    return stage_ms, n
 
 
 def main():
@@ -303,6 +322,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true",
                     help="skip the split-precision timing of the same workload")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the 1024-walker benchmark workload; c3: 8192 walkers with "
+                         "masses 1e3..1e9 Msun under CUDA-graph replay with autotuned tiles")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -314,11 +336,15 @@ def main():
 
     build.build()
     torch.cuda.set_device(local)
-    B = args.walkers
+    c3 = args.workload == "c3"
+    B = 8192 if c3 and args.walkers == 1024 else args.walkers
     g = W.GRID_C2
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B, device=local)
-    th = make_inputs(lisalike, like, g, 1 + 1000 * rank, B)
+    th = make_inputs(lisalike, like, g, (3 if c3 else 1) + 1000 * rank, B,
+                     (3.0, 9.0) if c3 else (5.0, 7.0))
     mode_bins, bins = work_units(like, th)
+    if c3:
+        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
 
     # a dedicated stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
@@ -334,8 +360,14 @@ def main():
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
-    lisalike.lisa_like_set_profiling(like.h, True)
-    lisalike.lisa_like_read_profile(like.h)
+    if c3:
+        stage_ms, ncalls = profile_once(lisalike, like, step)
+        lisalike.lisa_like_set_graphs(like.h, True)
+        step()
+        torch.cuda.synchronize()
+    else:
+        lisalike.lisa_like_set_profiling(like.h, True)
+        lisalike.lisa_like_read_profile(like.h)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
@@ -351,8 +383,10 @@ def main():
     barrier(world)
     ms_local = e0.elapsed_time(e1)
     clk = clocks.stop()
-    stage_ms, ncalls = lisalike.lisa_like_read_profile(like.h)
-    lisalike.lisa_like_set_profiling(like.h, False)
+    if not c3:
+        stage_ms, ncalls = lisalike.lisa_like_read_profile(like.h)
+        lisalike.lisa_like_set_profiling(like.h, False)
+    shape = lisalike.lisa_like_get_tune(like.h)
     ms = max_over_ranks(world, ms_local)
     value = world * B * args.steps / (ms * 1e-3)
     assert np.all(np.isfinite(lnL.cpu().numpy())), "non-finite ln L"
@@ -364,7 +398,7 @@ def main():
     lisalike.lisa_like_loglike(like.h, th, B, out, odh, ohh)
     barrier(world)
     t0 = time.perf_counter()
-    e2e_steps = max(2, args.steps // 2)
+    e2e_steps = max(1, args.steps // 2) if c3 else max(2, args.steps // 2)
     for _ in range(e2e_steps):
         lisalike.lisa_like_loglike(like.h, th, B, out, odh, ohh)
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
@@ -384,20 +418,24 @@ def main():
                                            "finish"), stage_ms)},
                 "hbm_gbs": BYTES_BIN * bins / (dense_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks().get("hbm_gbs")}
+    if c3:
+        roofline["note"] = "stage times from one profiled call before graph replay"
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "walkers_per_gpu": B, "n_bins": g.n_bins,
-                       "knots": 1024, "modes": 6, "precision": "fp64",
+            "config": {"workload": WORKLOAD_C3 if c3 else WORKLOAD, "walkers_per_gpu": B,
+                       "n_bins": g.n_bins, "knots": 1024, "modes": 6, "precision": "fp64",
+                       "graphs": c3, "tile": {"bins_per_thread": shape[0], "group": shape[1],
+                                              "blocks": shape[2]},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (data 227 MB, spline coefficients 1.6 GB)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     like.close()
     if not args.no_split:
         line["split_precision"] = time_split(lisalike, LisaLike, g, th, B, args, world, stream,
-                                             mode_bins, bins)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and B == 1024:
+                                             mode_bins, bins, graphs=c3)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and B == 1024 and not c3:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line))

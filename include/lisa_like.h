@@ -171,6 +171,27 @@ lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, double f0, do
                                       const double *d_params, int B, double *d_lnL,
                                       double *d_dh, double *d_hh, void *stream);
 
+/* Capture the whole per-call kernel sequence in a CUDA graph (on = 1) and replay it.
+ * The executable is cached for the last (B, parameter and output pointers) and
+ * rebuilt when they change; it runs on the handle's stream, ordered after and before
+ * the caller's stream by events.  Per-stage profiling does not apply to graph
+ * replays. */
+lisa_status lisa_like_set_graphs(lisa_like_t *h, int on);
+
+/* Tile shape of the fused dense kernel: `per_thread` consecutive bins per thread (the
+ * tile is 128 x per_thread bins) and `group` walkers sharing one staged data tile.
+ * Supported: (8,8), (4,8), (16,8) in split precision only, (8,1).  LISA_ERR_ARG
+ * otherwise.  out[3] of get_tune: per_thread, group, persistent blocks. */
+lisa_status lisa_like_set_tune(lisa_like_t *h, int per_thread, int group);
+lisa_status lisa_like_get_tune(const lisa_like_t *h, int *out);
+
+/* Autotuner: times every supported tile shape on the full call for these B host
+ * walkers (a representative sample is enough), keeps the fastest, and caches the
+ * choice per (n_bins, n_knots, precision) in the handle; later calls with the same
+ * key reuse it without timing.  out[3] (or NULL) receives the chosen shape.
+ * Requires set_data. */
+lisa_status lisa_like_autotune(lisa_like_t *h, const double *params, int B, int *out);
+
 /* Number of kernel launches the last loglike / loglike_device call enqueued. */
 int lisa_like_last_launches(const lisa_like_t *h);
 

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblisalike.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["lisa_like.cu", "stages.cu", "dense.cu", "split.cu", "noalloc.cu"]
+SOURCES = ["lisa_like.cu", "stages.cu", "plan.cu", "dense.cu", "split.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

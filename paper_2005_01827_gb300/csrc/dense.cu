@@ -209,6 +209,26 @@ cudaError_t launch_f64(const StageDims &d, const StageBufs &b, const double *bin
     return cudaGetLastError();
 }
 
+template <int C, int G>
+int occ_f64() {
+    const size_t smem = sizeof(double) * kBinDoubles * 128 * C + 16;
+    if (cudaFuncSetAttribute(dense_f64_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_f64_kernel<C, G>, 128, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int dense_f64_occupancy(int per_thread, int group) {
+    if (per_thread == 8 && group == 8) return occ_f64<8, 8>();
+    if (per_thread == 8 && group == 1) return occ_f64<8, 1>();
+    if (per_thread == 4 && group == 8) return occ_f64<4, 8>();
+    return 0;
+}
+
 cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
                              const DenseTune &t, cudaStream_t s) {
     if (t.threads != 128) return cudaErrorInvalidValue;

@@ -5,6 +5,8 @@
 
 namespace lisa {
 
+constexpr int kScratchRows = 11;  // rows of K doubles per (walker, mode) in mscratch
+
 // Device layout of one bin of the uploaded data: the FP64 dense kernel reads the
 // nine doubles w_A, w_E, w_T, (w d)_A re/im, (w d)_E re/im, (w d)_T re/im
 // (w = 4 df / S, Eqs. (3) and (11)); 72 bytes, 16-byte aligned rows of 2 bins.
@@ -24,12 +26,14 @@ struct StageBufs {
     const double *params;  // [B][11]
     int *valid;            // [B]
     double *tc;            // [B]
+    double *xpk;           // [B] peak of f^2 A_22 in M f
     int *band;             // [B][L][3]: active, j_lo, j_hi
     double *fedge;         // [B][L][2]
     double *fk;            // [B][L][K]
     int *kb;               // [B][L][K]: first dense bin with f_j >= f_k
     double *vals;          // [B][L][8][K]
-    double *mscratch;      // [B][L][8][K] second derivatives of the spline
+    double *mscratch;      // [B][L][11][K]: spline second derivatives of the 8 series, then
+                           // the shared factorisation (1/h, 1/pivot, normalised super-diagonal)
     double *coef;          // [B][L][K-1][8][4]
     int *wrange;           // [B][2] union of the walker's active mode ranges
     int *order;            // [B] walkers sorted by band (groups are runs of G entries)
@@ -65,6 +69,10 @@ cudaError_t launch_template(const StageDims &d, const StageBufs &b, double *out,
 cudaError_t launch_prep(const double *d, const double *psd, int N, double df, double *bins,
                         double *ddpart, int *bad, cudaStream_t s);
 int prep_blocks(int N);
+
+// Resident blocks per SM of a dense-kernel variant (0 if the variant does not exist).
+int dense_f64_occupancy(int per_thread, int group);
+int dense_split_occupancy(int per_thread, int group);
 
 // Largest number of (item, slot) partial-sum pairs a call with B walkers can produce.
 int64_t max_items(int B, int N, int tile_bins);

@@ -8,7 +8,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <map>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lisa_like.h"
@@ -47,7 +49,8 @@ struct lisa_like {
     SegRec *segs = nullptr;   // [max_batch][L][K-1] split-precision segment records
 
     // per-call buffers
-    double *params = nullptr, *tc = nullptr, *fedge = nullptr, *fk = nullptr, *vals = nullptr;
+    double *params = nullptr, *tc = nullptr, *xpk = nullptr, *fedge = nullptr, *fk = nullptr;
+    double *vals = nullptr;
     double *mscr = nullptr, *coef = nullptr, *part = nullptr, *out = nullptr;
     int *valid = nullptr, *band = nullptr, *kb = nullptr, *wrange = nullptr;
     int *order = nullptr, *slot_of = nullptr, *grange = nullptr;
@@ -57,6 +60,15 @@ struct lisa_like {
     int *h_err = nullptr;
     int last_launches = 0;
     std::vector<void *> deferred;  // device buffers that in-flight work may still touch
+    // CUDA graphs: one cached executable for the last (B, pointers) key
+    bool use_graphs = false;
+    cudaGraphExec_t gexec = nullptr;
+    int g_B = 0;
+    const void *g_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int g_launches = 0;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // tile shapes chosen by lisa_like_autotune, per (n_bins, K, precision)
+    std::map<std::tuple<int, int, int>, DenseTune> tuned;
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;  // kProfEvents events per profiled call
     int prof_calls = 0;
@@ -91,12 +103,13 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_batch(lisa_like_t *h) {
-    void *ptrs[] = {h->params, h->tc,    h->fedge,  h->fk,     h->vals,       h->mscr,
+    void *ptrs[] = {h->params, h->tc,    h->xpk,    h->fedge,  h->fk,  h->vals,  h->mscr,
                     h->coef,   h->out,   h->valid,  h->band,   h->kb,         h->wrange,
                     h->order,  h->slot_of, h->grange, h->item_start, h->counter, h->err_flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     h->order = h->slot_of = h->grange = h->err_flag = nullptr;
+    h->xpk = nullptr;
     if (h->segs) cudaFree(h->segs);
     h->segs = nullptr;
     h->params = h->tc = h->fedge = h->fk = h->vals = h->mscr = h->coef = h->out = nullptr;
@@ -112,13 +125,14 @@ lisa_status alloc_batch(lisa_like_t *h) {
     const size_t B = h->max_batch, L = h->L, K = h->K;
     LCK(dalloc(&h->params, B * kNPar), "device allocation (params)");
     LCK(dalloc(&h->tc, B), "device allocation (tc)");
+    LCK(dalloc(&h->xpk, B), "device allocation (peaks)");
     LCK(dalloc(&h->valid, B), "device allocation (valid)");
     LCK(dalloc(&h->band, B * L * 3), "device allocation (band)");
     LCK(dalloc(&h->fedge, B * L * 2), "device allocation (fedge)");
     LCK(dalloc(&h->fk, B * L * K), "device allocation (knots)");
     LCK(dalloc(&h->kb, B * L * K), "device allocation (knot bins)");
     LCK(dalloc(&h->vals, B * L * kNSeries * K), "device allocation (knot values)");
-    LCK(dalloc(&h->mscr, B * L * kNSeries * K), "device allocation (spline scratch)");
+    LCK(dalloc(&h->mscr, B * L * kScratchRows * K), "device allocation (spline scratch)");
     LCK(dalloc(&h->coef, B * L * (K - 1) * 32), "device allocation (spline coefficients)");
     LCK(dalloc(&h->wrange, 2 * B), "device allocation (ranges)");
     LCK(dalloc(&h->order, B), "device allocation (order)");
@@ -142,6 +156,7 @@ StageBufs bufs_of(const lisa_like_t *h, const double *params) {
     b.params = params;
     b.valid = h->valid;
     b.tc = h->tc;
+    b.xpk = h->xpk;
     b.band = h->band;
     b.fedge = h->fedge;
     b.fk = h->fk;
@@ -213,10 +228,68 @@ lisa_status prof_events(lisa_like_t *h, int c, cudaEvent_t **ev) {
     return LISA_OK;
 }
 
+// persistent grid of the dense kernel for a tile shape: every SM filled with resident blocks
+bool make_tune(const lisa_like_t *h, int per_thread, int group, DenseTune *t) {
+    const int occ = h->precision == LISA_PREC_SPLIT ? dense_split_occupancy(per_thread, group)
+                                                     : dense_f64_occupancy(per_thread, group);
+    if (occ <= 0) return false;
+    *t = {128, per_thread, h->n_sm * occ, group};
+    return true;
+}
+
+lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
+                    double *hh, cudaStream_t s, bool profile);
+
+void drop_graph(lisa_like_t *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_B = 0;
+}
+
 lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
                     double *hh, cudaStream_t s) {
+    if (!h->use_graphs) return enqueue(h, dparams, B, lnL, dh, hh, s, h->profiling);
+    const void *key[4] = {dparams, lnL, dh, hh};
+    const bool hit = h->gexec && h->g_B == B && std::equal(key, key + 4, h->g_key);
+    if (!hit) {
+        drop_graph(h);
+        cudaGraph_t g = nullptr;
+        LCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+        lisa_status st = enqueue(h, dparams, B, lnL, dh, hh, h->stream, false);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (st != LISA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            return cuda_fail(h, e, "graph instantiation");
+        }
+        h->g_B = B;
+        std::copy(key, key + 4, h->g_key);
+        h->g_launches = h->last_launches;
+    }
+    // the graph runs on the handle's stream, ordered after and before the caller's stream
+    if (s != h->stream) {
+        LCK(cudaEventRecord(h->ev_in, s), "cudaEventRecord");
+        LCK(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "cudaStreamWaitEvent");
+    }
+    LCK(cudaGraphLaunch(h->gexec, h->stream), "cudaGraphLaunch");
+    if (s != h->stream) {
+        LCK(cudaEventRecord(h->ev_out, h->stream), "cudaEventRecord");
+        LCK(cudaStreamWaitEvent(s, h->ev_out, 0), "cudaStreamWaitEvent");
+    }
+    h->last_launches = h->g_launches;
+    return LISA_OK;
+}
+
+lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
+                    double *hh, cudaStream_t s, bool profile) {
     cudaEvent_t *ev = nullptr;
-    if (h->profiling) {
+    if (profile) {
         if (h->prof_calls >= 4096) return fail(h, LISA_ERR_STATE, "read the profile first");
         lisa_status st = prof_events(h, h->prof_calls, &ev);
         if (st != LISA_OK) return st;
@@ -244,7 +317,7 @@ lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     LCK(launch_finish(d, b, h->tune.group, split ? 1 : 0, h->dd, lnL, dh, hh, s),
         "finish kernel launch");
     LCK(mark(6), "cudaEventRecord");
-    h->last_launches = split ? 6 : 5;
+    h->last_launches = split ? 7 : 6;  // band + knot kernels, splines, [segments], plan, dense, finish
     return LISA_OK;
 }
 
@@ -345,8 +418,15 @@ lisa_status lisa_like_create(const lisa_like_config *cfg, lisa_like_t **out) {
         }
         st = alloc_batch(h);
         if (st != LISA_OK) break;
-        // persistent grid: a fixed number of resident blocks per SM
-        h->tune.blocks = h->n_sm * 4;
+        if ((e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess) {
+            st = cuda_fail(h, e, "cudaEventCreate");
+            break;
+        }
+        if (!make_tune(h, 8, 8, &h->tune)) {
+            st = fail(h, LISA_ERR_CUDA, "dense kernel cannot be made resident on this device");
+            break;
+        }
     } while (0);
     if (st != LISA_OK) {
         g_create_error = h->err;
@@ -621,6 +701,84 @@ lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls) {
     return LISA_OK;
 }
 
+lisa_status lisa_like_set_graphs(lisa_like_t *h, int on) {
+    if (!h) return LISA_ERR_ARG;
+    h->use_graphs = on != 0;
+    if (!h->use_graphs) drop_graph(h);
+    return LISA_OK;
+}
+
+lisa_status lisa_like_set_tune(lisa_like_t *h, int per_thread, int group) {
+    if (!h) return LISA_ERR_ARG;
+    DenseTune t;
+    if (!make_tune(h, per_thread, group, &t))
+        return fail(h, LISA_ERR_ARG, "unsupported (per_thread, group) for this precision");
+    h->tune = t;
+    drop_graph(h);
+    return LISA_OK;
+}
+
+lisa_status lisa_like_get_tune(const lisa_like_t *h, int *out) {
+    if (!h || !out) return LISA_ERR_ARG;
+    out[0] = h->tune.per_thread;
+    out[1] = h->tune.group;
+    out[2] = h->tune.blocks;
+    return LISA_OK;
+}
+
+lisa_status lisa_like_autotune(lisa_like_t *h, const double *params, int B, int *out) {
+    if (!h) return LISA_ERR_ARG;
+    if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
+    if (B < 1 || B > h->max_batch || !params) return fail(h, LISA_ERR_ARG, "bad batch");
+    LCK(cudaSetDevice(h->device), "cudaSetDevice");
+    const auto key = std::make_tuple(h->N, h->K, h->precision);
+    auto it = h->tuned.find(key);
+    if (it == h->tuned.end()) {
+        cudaStream_t s = h->stream;
+        LCK(cudaMemcpyAsync(h->params, params, sizeof(double) * kNPar * B, cudaMemcpyHostToDevice, s),
+            "parameter upload");
+        const int cand[][2] = {{8, 8}, {4, 8}, {16, 8}, {8, 1}};
+        cudaEvent_t e0, e1;
+        LCK(cudaEventCreate(&e0), "cudaEventCreate");
+        LCK(cudaEventCreate(&e1), "cudaEventCreate");
+        float best = 3.4e38f;
+        DenseTune bt = h->tune;
+        lisa_status st = LISA_OK;
+        for (const auto &c : cand) {
+            DenseTune t;
+            if (!make_tune(h, c[0], c[1], &t)) continue;
+            h->tune = t;
+            st = enqueue(h, h->params, B, h->out, nullptr, nullptr, s, false);  // warm
+            if (st != LISA_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2 && st == LISA_OK; r++)
+                st = enqueue(h, h->params, B, h->out, nullptr, nullptr, s, false);
+            cudaEventRecord(e1, s);
+            if (st != LISA_OK) break;
+            st = wait_for(h, s);
+            if (st != LISA_OK) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = t;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != LISA_OK) return st;
+        it = h->tuned.emplace(key, bt).first;
+    }
+    h->tune = it->second;
+    drop_graph(h);
+    if (out) {
+        out[0] = h->tune.per_thread;
+        out[1] = h->tune.group;
+        out[2] = h->tune.blocks;
+    }
+    return LISA_OK;
+}
+
 int lisa_like_last_launches(const lisa_like_t *h) { return h ? h->last_launches : 0; }
 
 void lisa_like_destroy(lisa_like_t *h) {
@@ -638,6 +796,9 @@ void lisa_like_destroy(lisa_like_t *h) {
     if (h->bins) cudaFree(h->bins);
     if (h->bins32) cudaFree(h->bins32);
     if (h->part) cudaFree(h->part);
+    drop_graph(h);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     if (h->done) cudaEventDestroy(h->done);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

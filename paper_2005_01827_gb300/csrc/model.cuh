@@ -101,8 +101,9 @@ __device__ inline double peak_equation(const Source &s, double x) {
     return 5.0 / 6.0 + (2.0 / 3.0) * s.al2 * v * v + s.al3 * v * v * v - 6.0 * r6 / (1.0 + r6);
 }
 
-// Derive the walker constants; false for a walker outside the physical range.
-__device__ inline bool make_source(const double *th, double t0, Source &s) {
+// Derive the walker constants except the peak of f^2 A_22; false for a walker outside
+// the physical range.
+__device__ inline bool make_source_core(const double *th, double t0, Source &s) {
     for (int i = 0; i < kNPar; i++)
         if (!isfinite(th[i])) return false;
     const double mt = th[0], q = th[1], a1 = th[2], a2 = th[3], dl = th[4];
@@ -140,24 +141,35 @@ __device__ inline bool make_source(const double *th, double t0, Source &s) {
     s.phj = j.p;
     s.c2 = -0.5 * kXJoin * kXJoin * kXJoin * j.d2p;
     s.c1 = j.dp - s.c2 / (kXJoin * kXJoin);
-    // peak of f^2 A_22: bisection on the sign of its log-derivative
+    return true;
+}
+
+// peak of f^2 A_22 (t_coal is reached there, Sec. II): bisection on the sign of its
+// log-derivative over [x_RD/4, 2 x_RD]
+__device__ inline double find_peak(const Source &s) {
     double lo = 0.25 * s.xrd, hi = 2.0 * s.xrd;
-    if (peak_equation(s, lo) <= 0.0) {
-        s.xpk = lo;
-    } else if (peak_equation(s, hi) >= 0.0) {
-        s.xpk = hi;
-    } else {
-        for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; it++) {
-            const double mid = 0.5 * (lo + hi);
-            if (peak_equation(s, mid) > 0.0)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        s.xpk = 0.5 * (lo + hi);
+    if (peak_equation(s, lo) <= 0.0) return lo;
+    if (peak_equation(s, hi) >= 0.0) return hi;
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (peak_equation(s, mid) > 0.0)
+            lo = mid;
+        else
+            hi = mid;
     }
-    s.phpk = raw_phase(s, s.xpk);
-    s.dphpk = raw_slope(s, s.xpk);
+    return 0.5 * (lo + hi);
+}
+
+// align the (2,2) phase at the peak: t_22(f_peak) = t_coal and phi_22(f_peak) = 0
+__device__ inline void set_peak(Source &s, double xpk) {
+    s.xpk = xpk;
+    s.phpk = raw_phase(s, xpk);
+    s.dphpk = raw_slope(s, xpk);
+}
+
+__device__ inline bool make_source(const double *th, double t0, Source &s) {
+    if (!make_source_core(th, t0, s)) return false;
+    set_peak(s, find_peak(s));
     return true;
 }
 
@@ -225,6 +237,34 @@ __device__ inline double mode_phase(const Source &s, const Mode &md, double f) {
     const double x = mapped_x(s, md, f);
     const double p22 = raw_phase(s, x) - s.phpk - s.dphpk * (x - s.xpk);
     return 0.5 * md.m * p22 + phase_offset(md);
+}
+
+// A_lm(f), phi_lm(f) and t_lm(f) together (Eqs. (5), (6)), sharing one cube root:
+// x^(-7/6) = 1 / (x sqrt(x^(1/3))) with x^(1/3) = v / pi^(1/3)
+__device__ inline void mode_all(const Source &s, const Mode &md, double f, double &amp,
+                                double &phase, double &time) {
+    const double x = mapped_x(s, md, f);
+    const double v = cbrt(kPi * x);
+    const double ix = 1.0 / x;
+    double p, dp;
+    if (x <= kXJoin) {
+        const double iv = 1.0 / v;
+        const double iv2 = iv * iv, iv3 = iv2 * iv, iv5 = iv3 * iv2;
+        const double k = 1.0 / (128.0 * s.eta);
+        p = -3.0 * k * (iv5 + s.ps2 * iv3 + s.ps3 * iv2);
+        dp = k * ix * (5.0 * iv5 + 3.0 * s.ps2 * iv3 + 2.0 * s.ps3 * iv2);
+    } else {
+        p = s.phj + s.c1 * (x - kXJoin) - s.c2 * (ix - 1.0 / kXJoin);
+        dp = s.c1 + s.c2 * ix * ix;
+    }
+    time = s.tc - s.M / kTwoPi * (dp - s.dphpk);
+    phase = 0.5 * md.m * (p - s.phpk - s.dphpk * (x - s.xpk)) + phase_offset(md);
+    const double r = x / s.xrd;
+    const double r2 = r * r;
+    const double x16 = sqrt(v * 0.68278406325529568);  // x^(1/6); 0.6827... = pi^(-1/3)
+    const double a22 = s.amp0 * ix / x16 * exp(s.al2 * v * v + s.al3 * v * v * v) /
+                       (1.0 + r2 * r2 * r2);
+    amp = amp_ratio(s, md, v) * a22;
 }
 
 // -2Y_lm(iota, phi) for l = 2..4 in closed form; (l, m) with |m| from the mode table

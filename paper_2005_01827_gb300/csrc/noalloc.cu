@@ -38,7 +38,7 @@ void *g_addr[kMaxDevices] = {nullptr};
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t valid, tc, band, fedge, fk, kb, vals, mscr, coef, wrange, order, slot, grange, items,
+    size_t valid, tc, xpk, band, fedge, fk, kb, vals, mscr, coef, wrange, order, slot, grange, items,
         counter, err, part, end;
 };
 
@@ -52,12 +52,13 @@ Layout layout_for(size_t B, size_t L, size_t K, size_t items) {
     };
     o.valid = take(sizeof(int) * B);
     o.tc = take(sizeof(double) * B);
+    o.xpk = take(sizeof(double) * B);
     o.band = take(sizeof(int) * B * L * 3);
     o.fedge = take(sizeof(double) * B * L * 2);
     o.fk = take(sizeof(double) * B * L * K);
     o.kb = take(sizeof(int) * B * L * K);
     o.vals = take(sizeof(double) * B * L * kNSeries * K);
-    o.mscr = take(sizeof(double) * B * L * kNSeries * K);
+    o.mscr = take(sizeof(double) * B * L * kScratchRows * K);
     o.coef = take(sizeof(double) * B * L * (K - 1) * 32);
     o.wrange = take(sizeof(int) * 2 * B);
     o.order = take(sizeof(int) * B);
@@ -146,6 +147,7 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
     b.params = d_params;
     b.valid = reinterpret_cast<int *>(s8 + o.valid);
     b.tc = reinterpret_cast<double *>(s8 + o.tc);
+    b.xpk = reinterpret_cast<double *>(s8 + o.xpk);
     b.band = reinterpret_cast<int *>(s8 + o.band);
     b.fedge = reinterpret_cast<double *>(s8 + o.fedge);
     b.fk = reinterpret_cast<double *>(s8 + o.fk);

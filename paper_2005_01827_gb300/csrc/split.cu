@@ -438,6 +438,27 @@ cudaError_t launch_split(const StageDims &d, const StageBufs &b, const SegRec *s
     return cudaGetLastError();
 }
 
+template <int C, int G>
+int occ_split() {
+    const size_t smem = sizeof(float) * kBinFloats * 128 * C + 16;
+    if (cudaFuncSetAttribute(dense_split_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_split_kernel<C, G>, 128, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int dense_split_occupancy(int per_thread, int group) {
+    if (per_thread == 8 && group == 8) return occ_split<8, 8>();
+    if (per_thread == 8 && group == 1) return occ_split<8, 1>();
+    if (per_thread == 16 && group == 8) return occ_split<16, 8>();
+    if (per_thread == 4 && group == 8) return occ_split<4, 8>();
+    return 0;
+}
+
 cudaError_t launch_dense_split(const StageDims &d, const StageBufs &b, const SegRec *segs,
                                const float *bins, const DenseTune &t, cudaStream_t s) {
     if (t.threads != 128) return cudaErrorInvalidValue;

@@ -11,10 +11,73 @@ __device__ __forceinline__ double bin_freq(double f0, double df, int j) {
     return __dadd_rn(f0, __dmul_rn((double)j, df));
 }
 
+// ---------------------------------------------------------------------------- bands
+// One thread per (walker, mode): the walker constants, the peak of f^2 A_22 (thread of
+// mode 0 stores it), and the band (Sec. II: the cut where t_lm(f) < 0, and the
+// ringdown cut) with its integer dense-bin range.
+__global__ void __launch_bounds__(128) band_kernel(StageDims d, StageBufs b) {
+    const int wm = blockIdx.x * blockDim.x + threadIdx.x;
+    if (wm >= d.B * d.L) return;
+    const int w = wm / d.L, mi = wm % d.L;
+    const Mode md = {d.ml[mi], d.mm[mi]};
+    Source src;
+    const bool ok = make_source(b.params + (size_t)w * kNPar, d.t0, src);
+    int act = 0;
+    double lo = 0.0, hi = 0.0;
+    int jl = 0, jh = -1;
+    if (ok) {
+        const double fmn = d.f0;
+        const double fmx = bin_freq(d.f0, d.df, d.N - 1);
+        const double fcut = 0.5 * md.m * kXCut / src.M;
+        hi = fmx < fcut ? fmx : fcut;
+        if (hi > fmn * (1.0 + 1e-12)) {
+            act = 1;
+            if (mode_time(src, md, fmn) >= 0.0) {
+                lo = fmn;
+            } else if (mode_time(src, md, hi) < 0.0) {
+                act = 0;  // the mode ends before the observation starts
+            } else {
+                double a = fmn, c = hi;
+                for (int it = 0; it < 200 && c - a > 1e-14 * c; it++) {
+                    const double mid = 0.5 * (a + c);
+                    if (mode_time(src, md, mid) < 0.0)
+                        a = mid;
+                    else
+                        c = mid;
+                }
+                lo = c;
+            }
+            if (act && !(hi > lo * (1.0 + 1e-12))) act = 0;
+            if (act) {
+                const double gl = ceil((lo - d.f0) / d.df - 1e-9);
+                const double gh = floor((hi - d.f0) / d.df + 1e-9);
+                jl = gl < 0.0 ? 0 : (int)gl;
+                jh = gh > (double)(d.N - 1) ? d.N - 1 : (int)gh;
+                if (jl > jh) act = 0;
+            }
+        }
+    }
+    if (!act) {
+        jl = 0;
+        jh = -1;
+    }
+    int *bd = b.band + (size_t)wm * 3;
+    bd[0] = act;
+    bd[1] = jl;
+    bd[2] = jh;
+    b.fedge[(size_t)wm * 2] = lo;
+    b.fedge[(size_t)wm * 2 + 1] = hi;
+    if (mi == 0) {
+        b.valid[w] = ok ? 1 : 0;
+        b.tc[w] = ok ? src.tc : 0.0;
+        b.xpk[w] = ok ? src.xpk : 0.0;
+    }
+}
+
 // ---------------------------------------------------------------------------- knots
-// One block per (walker, mode).  Thread 0 derives the walker constants and the band
-// (Sec. II: the cut where t_lm(f) < 0, and the ringdown cut); all threads then fill
-// the K log-spaced knots (Sec. II.A: ~2^10 points) with A, phase + delay, and T.
+// One block per (walker, mode): thread 0 rebuilds the walker constants (the stored peak
+// spares the bisection) and the source frame; all threads then fill the K log-spaced
+// knots (Sec. II.A: ~2^10 points) with A, phase + delay, and T.
 __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
     const int wm = blockIdx.x;
     const int w = wm / d.L, mi = wm % d.L;
@@ -22,70 +85,17 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
     __shared__ Source src;
     __shared__ Frame frame;
     __shared__ cplx kp, kc;
-    __shared__ int active;
-    __shared__ double flo, fhi;
-
+    if (!b.band[(size_t)wm * 3]) return;  // inactive modes (and invalid walkers) have no knots
     if (threadIdx.x == 0) {
-        const bool ok = make_source(b.params + (size_t)w * kNPar, d.t0, src);
-        int act = 0;
-        double lo = 0.0, hi = 0.0;
-        int jl = 0, jh = -1;
-        if (ok) {
-            make_frame(src, frame);
-            pol_weights(src, md, kp, kc);
-            const double fmn = d.f0;
-            const double fmx = bin_freq(d.f0, d.df, d.N - 1);
-            const double fcut = 0.5 * md.m * kXCut / src.M;
-            hi = fmx < fcut ? fmx : fcut;
-            if (hi > fmn * (1.0 + 1e-12)) {
-                act = 1;
-                if (mode_time(src, md, fmn) >= 0.0) {
-                    lo = fmn;
-                } else if (mode_time(src, md, hi) < 0.0) {
-                    act = 0;  // the mode ends before the observation starts
-                } else {
-                    double a = fmn, c = hi;
-                    for (int it = 0; it < 200 && c - a > 1e-14 * c; it++) {
-                        const double mid = 0.5 * (a + c);
-                        if (mode_time(src, md, mid) < 0.0)
-                            a = mid;
-                        else
-                            c = mid;
-                    }
-                    lo = c;
-                }
-                if (act && !(hi > lo * (1.0 + 1e-12))) act = 0;
-                if (act) {
-                    const double gl = ceil((lo - d.f0) / d.df - 1e-9);
-                    const double gh = floor((hi - d.f0) / d.df + 1e-9);
-                    jl = gl < 0.0 ? 0 : (int)gl;
-                    jh = gh > (double)(d.N - 1) ? d.N - 1 : (int)gh;
-                    if (jl > jh) act = 0;
-                }
-            }
-        }
-        if (!act) {
-            jl = 0;
-            jh = -1;
-        }
-        active = act;
-        flo = lo;
-        fhi = hi;
-        int *bd = b.band + (size_t)wm * 3;
-        bd[0] = act;
-        bd[1] = jl;
-        bd[2] = jh;
-        b.fedge[(size_t)wm * 2] = lo;
-        b.fedge[(size_t)wm * 2 + 1] = hi;
-        if (mi == 0) {
-            b.valid[w] = ok ? 1 : 0;
-            b.tc[w] = ok ? src.tc : 0.0;
-        }
+        make_source_core(b.params + (size_t)w * kNPar, d.t0, src);
+        set_peak(src, b.xpk[w]);
+        make_frame(src, frame);
+        pol_weights(src, md, kp, kc);
     }
     __syncthreads();
-    if (!active) return;
 
     const int K = d.K;
+    const double flo = b.fedge[(size_t)wm * 2], fhi = b.fedge[(size_t)wm * 2 + 1];
     const double r = log(fhi / flo);
     double *fkm = b.fk + (size_t)wm * K;
     int *kbm = b.kb + (size_t)wm * K;
@@ -99,12 +109,13 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
         while (j > 0 && bin_freq(d.f0, d.df, j - 1) >= f) j--;
         while (j < d.N && bin_freq(d.f0, d.df, j) < f) j++;
         kbm[k] = j;
-        const double t = mode_time(src, md, f);
+        double amp, ph, t;
+        mode_all(src, md, f, amp, ph, t);
         cplx T[3];
         double dly;
         tdi_transfer(frame, kp, kc, f, t, T, &dly);
-        vm[0 * K + k] = mode_amp(src, md, f);
-        vm[1 * K + k] = mode_phase(src, md, f) + dly;
+        vm[0 * K + k] = amp;
+        vm[1 * K + k] = ph + dly;
         vm[2 * K + k] = T[0].re;
         vm[3 * K + k] = T[0].im;
         vm[4 * K + k] = T[1].re;
@@ -115,67 +126,85 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
 }
 
 cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    band_kernel<<<(d.B * d.L + 127) / 128, 128, 0, s>>>(d, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     knot_kernel<<<d.B * d.L, 128, 0, s>>>(d, b);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- splines
-// One warp per (walker, mode).  Not-a-knot cubic splines (the Scipy-type tridiagonal
-// solve of Sec. II.A) for the 8 series share one matrix: lane 0 factorises it once,
-// lanes 0..7 each sweep one right-hand side, then all lanes emit the per-segment
-// coefficients.  Unknowns are the second derivatives M_1..M_{K-2}; not-a-knot
-// eliminates M_0 and M_{K-1}.
-__global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
-    extern __shared__ double sh[];
-    const int wm = blockIdx.x;
-    if (!b.band[(size_t)wm * 3]) return;
-    const int K = d.K, n = K;
-    double *hh = sh;            // [K-1] knot spacings
-    double *ih = sh + K;        // [K-1] their reciprocals
-    double *dinv = sh + 2 * K;  // [K] reciprocal Thomas pivots
-    double *cpr = sh + 3 * K;   // [K] normalised super-diagonal
-    double *sub = sh + 4 * K;   // [K] sub-diagonal
-    const double *x = b.fk + (size_t)wm * K;
-    const double *y = b.vals + (size_t)wm * kNSeries * K;
-    double *Mv = b.mscratch + (size_t)wm * kNSeries * K;
-    const int lane = threadIdx.x;
+// Not-a-knot cubic splines (the Scipy-type tridiagonal solve of Sec. II.A).  Unknowns
+// are the second derivatives M_1..M_{K-2}; not-a-knot eliminates M_0 and M_{K-1}.  The
+// 8 series of one (walker, mode) share the matrix.  A block owns 32 systems and every
+// lane one system, so the serial recurrences keep all 32 lanes busy (GB300's FP64 pipe
+// spends a full warp's time on every FP64 instruction whatever the active mask): warp 0
+// factorises the 32 matrices, warp q sweeps series q of the 32 systems, then all
+// threads emit the per-segment coefficients.  The factorisation lives in global
+// scratch rows next to the second derivatives.
+constexpr int kSplineSystems = 32;
 
-    for (int k = lane; k < n - 1; k += 32) {
-        hh[k] = x[k + 1] - x[k];
-        ih[k] = 1.0 / hh[k];
-    }
-    __syncwarp();
-    if (lane == 0) {
+__global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
+    const int K = d.K, n = K;
+    const int nsys = d.B * d.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = blockIdx.x * kSplineSystems + lane;
+    const bool mine = wm < nsys && b.band[(size_t)wm * 3];
+    const double *x = b.fk + (size_t)wm * K;
+    double *Mv = b.mscratch + (size_t)wm * kScratchRows * K;
+    double *ih = Mv + (size_t)kNSeries * K;  // 1 / h
+    double *dinv = ih + K;                   // 1 / pivot
+    double *cpr = dinv + K;                  // normalised super-diagonal
+    if (warp == 0 && mine) {
+        double hprev = x[1] - x[0], hcur;
+        const double ih0 = 1.0 / hprev;
+        ih[0] = ih0;
+        double cprev = 0.0;
+        double ihprev = ih0;  // 1 / h_{i-1}
         for (int i = 1; i <= n - 2; i++) {
-            double dia = 2.0 * (hh[i - 1] + hh[i]);
-            double sup = hh[i];
-            double sb = hh[i - 1];
+            hcur = x[i + 1] - x[i];
+            const double ihc = 1.0 / hcur;
+            ih[i] = ihc;
+            double dia = 2.0 * (hprev + hcur);
+            double sup = hcur;
+            double sb = hprev;
             if (i == 1) {
-                dia += hh[0] * (hh[0] + hh[1]) * ih[1];
-                sup -= hh[0] * hh[0] * ih[1];
+                dia += hprev * (hprev + hcur) * ihc;
+                sup -= hprev * hprev * ihc;
             }
             if (i == n - 2) {
-                dia += hh[n - 2] * (hh[n - 3] + hh[n - 2]) * ih[n - 3];
-                sb -= hh[n - 2] * hh[n - 2] * ih[n - 3];
+                dia += hcur * (hprev + hcur) * ihprev;
+                sb -= hcur * hcur * ihprev;
             }
-            const double pv = (i == 1) ? dia : dia - sb * cpr[i - 1];
+            const double pv = (i == 1) ? dia : dia - sb * cprev;
             const double inv = 1.0 / pv;
             dinv[i] = inv;
-            cpr[i] = sup * inv;
-            sub[i] = sb;
+            cprev = sup * inv;
+            cpr[i] = cprev;
+            hprev = hcur;
+            ihprev = ihc;
         }
     }
-    __syncwarp();
-    if (lane < kNSeries) {
-        const double *yq = y + (size_t)lane * K;
-        double *Mq = Mv + (size_t)lane * K;
+    __syncthreads();
+    if (mine) {
+        const int q = warp;  // series
+        const double *yq = b.vals + ((size_t)wm * kNSeries + q) * K;
+        double *Mq = Mv + (size_t)q * K;
         double prev = 0.0;
         double dprev = (yq[1] - yq[0]) * ih[0];
+        double ylast = yq[1];
         for (int i = 1; i <= n - 2; i++) {
-            const double dcur = (yq[i + 1] - yq[i]) * ih[i];
+            const double ynext = yq[i + 1];
+            const double dcur = (ynext - ylast) * ih[i];
+            ylast = ynext;
             const double rhs = 6.0 * (dcur - dprev);
             dprev = dcur;
-            const double rp = (rhs - sub[i] * prev) * dinv[i];
+            double sb = x[i] - x[i - 1];
+            if (i == n - 2) {
+                const double hb = x[n - 1] - x[n - 2];
+                sb -= hb * hb * ih[n - 3];
+            }
+            const double rp = (i == 1) ? rhs * dinv[1] : (rhs - sb * prev) * dinv[i];
             Mq[i] = rp;
             prev = rp;
         }
@@ -184,18 +213,26 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
             nxt = Mq[i] - cpr[i] * nxt;
             Mq[i] = nxt;
         }
-        Mq[0] = ((hh[0] + hh[1]) * Mq[1] - hh[0] * Mq[2]) * ih[1];
-        Mq[n - 1] = ((hh[n - 3] + hh[n - 2]) * Mq[n - 2] - hh[n - 2] * Mq[n - 3]) * ih[n - 3];
+        const double h0 = x[1] - x[0], h1 = x[2] - x[1];
+        const double ha = x[n - 2] - x[n - 3], hb = x[n - 1] - x[n - 2];
+        Mq[0] = ((h0 + h1) * Mq[1] - h0 * Mq[2]) * ih[1];
+        Mq[n - 1] = ((ha + hb) * Mq[n - 2] - hb * Mq[n - 3]) * ih[n - 3];
     }
-    __syncwarp();
-    double *cm = b.coef + (size_t)wm * (K - 1) * 32;
-    for (int t = lane; t < (n - 1) * kNSeries; t += 32) {
-        const int sgm = t / kNSeries, q = t % kNSeries;
-        const double *yq = y + (size_t)q * K;
-        const double *Mq = Mv + (size_t)q * K;
-        const double h = hh[sgm], hi = ih[sgm];
+    __syncthreads();
+    // coefficients: per segment and series of the block's systems
+    const int per_sys = (n - 1) * kNSeries;
+    for (int t = threadIdx.x; t < kSplineSystems * per_sys; t += blockDim.x) {
+        const int sys = t / per_sys, rem = t % per_sys;
+        const int w2 = blockIdx.x * kSplineSystems + sys;
+        if (w2 >= nsys || !b.band[(size_t)w2 * 3]) continue;
+        const int sgm = rem / kNSeries, q = rem % kNSeries;
+        const double *x2 = b.fk + (size_t)w2 * K;
+        const double *M2 = b.mscratch + (size_t)w2 * kScratchRows * K;
+        const double *yq = b.vals + ((size_t)w2 * kNSeries + q) * K;
+        const double *Mq = M2 + (size_t)q * K;
+        const double h = x2[sgm + 1] - x2[sgm], hi = M2[(size_t)kNSeries * K + sgm];
         const double m0 = Mq[sgm], m1 = Mq[sgm + 1];
-        double *c = cm + (size_t)sgm * 32 + q * 4;
+        double *c = b.coef + ((size_t)w2 * (K - 1) + sgm) * 32 + q * 4;
         c[0] = yq[sgm];
         c[1] = (yq[sgm + 1] - yq[sgm]) * hi - h * (2.0 * m0 + m1) * (1.0 / 6.0);
         c[2] = 0.5 * m0;
@@ -204,14 +241,8 @@ __global__ void __launch_bounds__(32) spline_kernel(StageDims d, StageBufs b) {
 }
 
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
-    const size_t smem = sizeof(double) * 5 * (size_t)d.K;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(spline_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    spline_kernel<<<d.B * d.L, 32, smem, s>>>(d, b);
+    const int nsys = d.B * d.L;
+    spline_kernel<<<(nsys + kSplineSystems - 1) / kSplineSystems, 256, 0, s>>>(d, b);
     return cudaGetLastError();
 }
 

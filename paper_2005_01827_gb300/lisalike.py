@@ -29,6 +29,7 @@ SYMBOLS = (
     "lisa_like_stage_knots", "lisa_like_stage_coeffs", "lisa_dl_from_z", "lisa_psd_aet",
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
+    "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
 )
 NOALLOC_SCRATCH_BYTES = 4194304
 NOALLOC_MAX_WALKER_MODE_KNOTS = 8192
@@ -97,6 +98,15 @@ def load(path: str = LIB_PATH):
     L.lisa_like_read_profile.restype = i
     L.lisa_like_loglike_noalloc.argtypes = [cfgp, d, d, i64, vp, d, vp, i, vp, vp, vp, vp]
     L.lisa_like_loglike_noalloc.restype = i
+    ip = C.POINTER(C.c_int)
+    L.lisa_like_set_graphs.argtypes = [vp, i]
+    L.lisa_like_set_graphs.restype = i
+    L.lisa_like_set_tune.argtypes = [vp, i, i]
+    L.lisa_like_set_tune.restype = i
+    L.lisa_like_get_tune.argtypes = [vp, ip]
+    L.lisa_like_get_tune.restype = i
+    L.lisa_like_autotune.argtypes = [vp, vp, i, ip]
+    L.lisa_like_autotune.restype = i
     L.lisa_like_last_launches.argtypes = [vp]
     L.lisa_like_last_launches.restype = i
     L.lisa_like_destroy.argtypes = [vp]
@@ -201,6 +211,28 @@ def lisa_like_loglike_noalloc(cfg, f0, df, n_bins, d_bins, dd, d_params, B, d_ln
     _check(load().lisa_like_loglike_noalloc(C.byref(cfg), f0, df, n_bins, _ptr(d_bins), dd,
                                             _ptr(d_params), B, _ptr(d_lnL), _ptr(d_dh),
                                             _ptr(d_hh), s))
+
+
+def lisa_like_set_graphs(h, on: bool):
+    _check(load().lisa_like_set_graphs(h, int(bool(on))), h)
+
+
+def lisa_like_set_tune(h, per_thread: int, group: int):
+    _check(load().lisa_like_set_tune(h, per_thread, group), h)
+
+
+def lisa_like_get_tune(h):
+    out = (C.c_int * 3)()
+    _check(load().lisa_like_get_tune(h, out), h)
+    return tuple(out)
+
+
+def lisa_like_autotune(h, params, B):
+    """Time the supported dense tile shapes on these walkers and keep the fastest."""
+    out = (C.c_int * 3)()
+    p = _f64(params)
+    _check(load().lisa_like_autotune(h, _ptr(p), B, out), h)
+    return tuple(out)
 
 
 def lisa_like_last_launches(h) -> int:
