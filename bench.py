@@ -39,12 +39,12 @@ WORKLOAD = ("1024 walkers, 6 modes (2,2),(3,3),(4,4),(2,1),(3,2),(4,3), K=1024 k
 WORKLOAD_C3 = ("8192 walkers with M_T log-uniform in [1e3, 1e9] Msun, 6 modes, K=1024 knots, "
                "1-yr grid (3155445 bins), A/E/T, FP64, CUDA-graph replay, autotuned tiles, "
                "Binary-1 injection + seeded noise")
-# algorithmic FP64 work (see the design notes): per (walker, mode, active bin) 8 cubic
-# Horner evaluations (48), the segment offset (1), the t_coal ramp (2), A e^{i phi} (2),
-# three complex transfer products (18), the mode sum (6) = 77 flops plus one sincos
-# counted as 40 flops (a reduction and two polynomials, 20 FMA); per (walker, bin)
-# f_j (2) and the three-channel integrand (27) = 29 flops.
-FLOP_MODE_BIN = 77 + 40
+# algorithmic work (see the design notes): per (walker, mode, active bin) 8 cubic Horner
+# evaluations (48), the segment offset (1), the t_coal ramp (2), e^{i phi} (20: a table
+# entry rotated by sine and cosine polynomials of the remaining angle), A e^{i phi} (2),
+# three complex transfer products accumulated into the mode sum (24) = 97 flops; per
+# (walker, bin) f_j (2) and the three-channel integrand (27) = 29 flops.
+FLOP_MODE_BIN = 48 + 1 + 2 + 20 + 2 + 24
 FLOP_BIN = 29
 # data bytes streamed per bin by a walker tile (w and w*d for A, E, T, FP64) and the
 # spline coefficients per segment (8 series x 4 doubles)

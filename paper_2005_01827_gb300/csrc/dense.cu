@@ -7,6 +7,11 @@
 // One bulk copy (TMA) stages the tile's w and w d (72 bytes per bin) in shared memory;
 // every walker of the group then reads them from there.  Blocks are persistent and pull
 // items from a counter.
+//
+// The phase phi - 2 pi f t_coal of each mode advances from bin to bin by exact 64-bit
+// fixed-point forward differences (anchored per spline segment by an FP64 prologue),
+// and e^{i phase} is a 1024-entry FP64 table entry rotated by a short polynomial in the
+// remaining angle (< 2 pi / 1024): every floating-point operation stays FP64.
 #include "kernels.h"
 #include "model.cuh"
 #include "tma.cuh"
@@ -29,16 +34,53 @@ __device__ __forceinline__ int segment_of(const int *__restrict__ kb, int K, int
     return lo;
 }
 
-// Horner evaluation of the 8 cubics of one segment at offset x.
+// Horner evaluation of the amplitude and transfer cubics (series 0, 2..7) of one segment
+// at offset x; the phase series is carried by the fixed-point recurrence instead.
 __device__ __forceinline__ void eval_segment(const double *__restrict__ c, double x,
                                              double v[kNSeries]) {
     const double2 *c2 = reinterpret_cast<const double2 *>(c);
 #pragma unroll
     for (int q = 0; q < kNSeries; q++) {
+        if (q == 1) continue;
         const double2 lo = __ldg(c2 + 2 * q);
         const double2 hi = __ldg(c2 + 2 * q + 1);
         v[q] = fma(x, fma(x, fma(x, hi.y, hi.x), lo.y), lo.x);
     }
+}
+
+struct Phase64 {
+    unsigned long long ph, d1, d2, d3;
+};
+
+// fixed-point forward differences of a segment's phase moved to bin n of the segment
+__device__ __forceinline__ Phase64 phase64_at(const unsigned long long *__restrict__ r, int n) {
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(r));
+    const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(r) + 1);
+    const long long nn = n;
+    const unsigned long long c1 = (unsigned long long)nn;
+    const unsigned long long c2 = (unsigned long long)(nn * (nn - 1)) >> 1;
+    const unsigned long long c3 = (c2 * (unsigned long long)(nn - 2)) * 0xAAAAAAAAAAAAAAABull;
+    Phase64 p;
+    p.ph = a.x + c1 * a.y + c2 * b.x + c3 * b.y;
+    p.d1 = a.y + c1 * b.x + c2 * b.y;
+    p.d2 = b.x + c1 * b.y;
+    p.d3 = b.y;
+    return p;
+}
+
+// e^{2 pi i ph / 2^64} in FP64: the top 10 bits select e^{2 pi i k / 1024}, the next 52
+// bits give r < 2 pi / 1024, and sin r, cos r are Taylor polynomials whose truncation
+// error is below 1e-17
+__device__ __forceinline__ void phasor64(unsigned long long ph, const double2 *__restrict__ tab,
+                                         double &zr, double &zi) {
+    const double2 t = tab[ph >> 54];
+    const double u = __longlong_as_double(0x3ff0000000000000ull | ((ph << 10) >> 12)) - 1.0;
+    const double r = u * 6.1359231515425647e-03;  // 2 pi / 1024
+    const double r2 = r * r;
+    const double sn = r * fma(r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+    const double cs = fma(r2, fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    zr = fma(t.x, cs, -t.y * sn);
+    zi = fma(t.x, sn, t.y * cs);
 }
 
 // group of a work item: largest g with item_start[g] <= item
@@ -54,17 +96,26 @@ __device__ __forceinline__ int group_of(const int *__restrict__ item_start, int 
     return lo;
 }
 
+constexpr int kTab64 = 1024;
+
 template <int C, int G>
 __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b,
+                                                        const unsigned long long *__restrict__ segs,
                                                         const double *__restrict__ bins,
                                                         int tile_bins) {
     extern __shared__ __align__(128) unsigned char smem[];
-    double *sbin = reinterpret_cast<double *>(smem);  // [tile_bins][9]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + sizeof(double) * kBinDoubles * tile_bins);
+    double2 *tab = reinterpret_cast<double2 *>(smem);                       // [1024]
+    double *sbin = reinterpret_cast<double *>(smem + sizeof(double2) * kTab64);  // [tile][9]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + sizeof(double2) * kTab64 +
+                                                 sizeof(double) * kBinDoubles * tile_bins);
     __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
-    __shared__ double s_tc[G];
     __shared__ double red[2][4];
     const int tid = threadIdx.x;
+    for (int k = tid; k < kTab64; k += blockDim.x) {
+        double sn, cs;
+        sincospi((double)k / (kTab64 / 2), &sn, &cs);
+        tab[k] = make_double2(cs, sn);
+    }
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
     const int ng = n_groups(d.B, G);
@@ -92,9 +143,7 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
             sbin[full * kBinDoubles + tid] = bins[((size_t)J0 + full) * kBinDoubles + tid];
         if (tid < G) {
             const int i = g * G + tid;
-            const int w = i < d.B ? b.order[i] : -1;
-            s_walker[tid] = w;
-            s_tc[tid] = w >= 0 ? kTwoPi * b.tc[w] : 0.0;
+            s_walker[tid] = i < d.B ? b.order[i] : -1;
         }
         if (tid < G * kMaxModes) {
             const int k = tid / kMaxModes, mi = tid % kMaxModes;
@@ -130,14 +179,22 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
                 continue;
             }
             const int j0 = J0 + tid * C;
-            const double wtc = s_tc[k];
-            int seg[kMaxModes];
+            int seg[kMaxModes], knext[kMaxModes];
+            Phase64 ph[kMaxModes];
 #pragma unroll
             for (int mi = 0; mi < kMaxModes; mi++) {
                 seg[mi] = 0;
+                knext[mi] = 0x7fffffff;
+                ph[mi] = Phase64{0, 0, 0, 0};
                 const int jj = max(j0, s_lo[k][mi]);
-                if (mi < d.L && jj <= s_hi[k][mi] && jj < min(j0 + C, Jend))
-                    seg[mi] = segment_of(b.kb + ((size_t)w * d.L + mi) * K, K, jj);
+                if (mi < d.L && jj <= s_hi[k][mi] && jj < min(j0 + C, Jend)) {
+                    const size_t wm = (size_t)w * d.L + mi;
+                    const int *kbm = b.kb + wm * K;
+                    const int s = segment_of(kbm, K, jj);
+                    seg[mi] = s;
+                    knext[mi] = (s < K - 2) ? __ldg(kbm + s + 1) : 0x7fffffff;
+                    ph[mi] = phase64_at(segs + 4 * (wm * (K - 1) + s), jj - __ldg(kbm + s));
+                }
             }
             double dh = 0.0, hh = 0.0;
             for (int i = 0; i < C; i++) {
@@ -149,15 +206,23 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
                 for (int mi = 0; mi < kMaxModes; mi++) {
                     if (mi >= d.L || j < s_lo[k][mi] || j > s_hi[k][mi]) continue;
                     const size_t wm = (size_t)w * d.L + mi;
-                    const int *kbm = b.kb + wm * K;
-                    int s = seg[mi];
-                    while (s < K - 2 && j >= __ldg(kbm + s + 1)) s++;
-                    seg[mi] = s;
+                    if (j >= knext[mi]) {  // into the next segment: new anchor
+                        const int *kbm = b.kb + wm * K;
+                        int s = seg[mi];
+                        while (s < K - 2 && j >= __ldg(kbm + s + 1)) s++;
+                        seg[mi] = s;
+                        knext[mi] = (s < K - 2) ? __ldg(kbm + s + 1) : 0x7fffffff;
+                        ph[mi] = phase64_at(segs + 4 * (wm * (K - 1) + s), j - __ldg(kbm + s));
+                    }
+                    const int s = seg[mi];
                     const double x = f - __ldg(b.fk + wm * K + s);
                     double v[kNSeries];
                     eval_segment(b.coef + (wm * (K - 1) + s) * 32, x, v);
-                    double sn, cs;
-                    sincos(fma(-wtc, f, v[1]), &sn, &cs);
+                    double cs, sn;
+                    phasor64(ph[mi].ph, tab, cs, sn);
+                    ph[mi].ph += ph[mi].d1;
+                    ph[mi].d1 += ph[mi].d2;
+                    ph[mi].d2 += ph[mi].d3;
                     const double zr = v[0] * cs, zi = v[0] * sn;
                     hr0 = fma(v[2], zr, fma(-v[3], zi, hr0));
                     hi0 = fma(v[2], zi, fma(v[3], zr, hi0));
@@ -197,21 +262,26 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
     }
 }
 
+template <int C>
+constexpr size_t f64_smem() {
+    return sizeof(double2) * kTab64 + sizeof(double) * kBinDoubles * 128 * C + 16;
+}
+
 template <int C, int G>
-cudaError_t launch_f64(const StageDims &d, const StageBufs &b, const double *bins, int blocks,
-                       cudaStream_t s) {
+cudaError_t launch_f64(const StageDims &d, const StageBufs &b, const unsigned long long *segs,
+                       const double *bins, int blocks, cudaStream_t s) {
     const int tile = 128 * C;
-    const size_t smem = sizeof(double) * kBinDoubles * tile + 16;
+    const size_t smem = f64_smem<C>();
     cudaError_t e = cudaFuncSetAttribute(dense_f64_kernel<C, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dense_f64_kernel<C, G><<<blocks, 128, smem, s>>>(d, b, bins, tile);
+    dense_f64_kernel<C, G><<<blocks, 128, smem, s>>>(d, b, segs, bins, tile);
     return cudaGetLastError();
 }
 
 template <int C, int G>
 int occ_f64() {
-    const size_t smem = sizeof(double) * kBinDoubles * 128 * C + 16;
+    const size_t smem = f64_smem<C>();
     if (cudaFuncSetAttribute(dense_f64_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
@@ -226,15 +296,18 @@ int dense_f64_occupancy(int per_thread, int group) {
     if (per_thread == 8 && group == 8) return occ_f64<8, 8>();
     if (per_thread == 8 && group == 1) return occ_f64<8, 1>();
     if (per_thread == 4 && group == 8) return occ_f64<4, 8>();
+    if (per_thread == 4 && group == 1) return occ_f64<4, 1>();
     return 0;
 }
 
-cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
+cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b,
+                             const unsigned long long *segs, const double *bins,
                              const DenseTune &t, cudaStream_t s) {
     if (t.threads != 128) return cudaErrorInvalidValue;
-    if (t.per_thread == 8 && t.group == 8) return launch_f64<8, 8>(d, b, bins, t.blocks, s);
-    if (t.per_thread == 8 && t.group == 1) return launch_f64<8, 1>(d, b, bins, t.blocks, s);
-    if (t.per_thread == 4 && t.group == 8) return launch_f64<4, 8>(d, b, bins, t.blocks, s);
+    if (t.per_thread == 8 && t.group == 8) return launch_f64<8, 8>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 8 && t.group == 1) return launch_f64<8, 1>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 4 && t.group == 8) return launch_f64<4, 8>(d, b, segs, bins, t.blocks, s);
+    if (t.per_thread == 4 && t.group == 1) return launch_f64<4, 1>(d, b, segs, bins, t.blocks, s);
     return cudaErrorInvalidValue;
 }
 

@@ -59,7 +59,12 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, int group,
                         cudaStream_t s);
-cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b, const double *bins,
+// FP64 path: per segment, the full phase and its first three forward differences at the
+// segment's first bin as 64-bit fixed-point fractions of a turn ([B][L][K-1][4]).
+cudaError_t launch_phaseprep(const StageDims &d, const StageBufs &b, unsigned long long *phases,
+                             cudaStream_t s);
+cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b,
+                             const unsigned long long *phases, const double *bins,
                              const DenseTune &t, cudaStream_t s);
 // split = 0: parts hold (<d|h>, <h|h>); split = 1: (sum |h|^2 - 2 Re(d h*), <h|h>)
 cudaError_t launch_finish(const StageDims &d, const StageBufs &b, int group, int split, double dd,

@@ -47,6 +47,7 @@ struct lisa_like {
     double *bins = nullptr;   // [N][9] FP64 staged data
     float *bins32 = nullptr;  // [N][9] FP32 whitened data (split precision)
     SegRec *segs = nullptr;   // [max_batch][L][K-1] split-precision segment records
+    unsigned long long *phases = nullptr;  // [max_batch][L][K-1][4] FP64-path phase anchors
 
     // per-call buffers
     double *params = nullptr, *tc = nullptr, *xpk = nullptr, *fedge = nullptr, *fk = nullptr;
@@ -111,7 +112,9 @@ void free_batch(lisa_like_t *h) {
     h->order = h->slot_of = h->grange = h->err_flag = nullptr;
     h->xpk = nullptr;
     if (h->segs) cudaFree(h->segs);
+    if (h->phases) cudaFree(h->phases);
     h->segs = nullptr;
+    h->phases = nullptr;
     h->params = h->tc = h->fedge = h->fk = h->vals = h->mscr = h->coef = h->out = nullptr;
     h->valid = h->band = h->kb = h->wrange = h->item_start = h->counter = nullptr;
     if (h->h_params) cudaFreeHost(h->h_params);
@@ -145,6 +148,8 @@ lisa_status alloc_batch(lisa_like_t *h) {
     LCK(dalloc(&h->out, 3 * B), "device allocation (outputs)");
     if (h->precision == LISA_PREC_SPLIT)
         LCK(dalloc(&h->segs, B * L * (K - 1)), "device allocation (split segments)");
+    else
+        LCK(dalloc(&h->phases, B * L * (K - 1) * 4), "device allocation (phase anchors)");
     LCK(cudaMallocHost(&h->h_params, sizeof(double) * B * kNPar), "pinned allocation");
     LCK(cudaMallocHost(&h->h_out, sizeof(double) * 3 * B), "pinned allocation");
     LCK(cudaMallocHost(&h->h_err, sizeof(int)), "pinned allocation");
@@ -305,19 +310,22 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     LCK(mark(1), "cudaEventRecord");
     LCK(launch_spline(d, b, s), "spline kernel launch");
     LCK(mark(2), "cudaEventRecord");
-    if (split) LCK(launch_segprep(d, b, h->segs, s), "segment kernel launch");
+    if (split)
+        LCK(launch_segprep(d, b, h->segs, s), "segment kernel launch");
+    else
+        LCK(launch_phaseprep(d, b, h->phases, s), "segment kernel launch");
     LCK(mark(3), "cudaEventRecord");
     LCK(launch_plan(d, b, tile, h->tune.group, s), "plan kernel launch");
     LCK(mark(4), "cudaEventRecord");
     if (split)
         LCK(launch_dense_split(d, b, h->segs, h->bins32, h->tune, s), "dense kernel launch");
     else
-        LCK(launch_dense_f64(d, b, h->bins, h->tune, s), "dense kernel launch");
+        LCK(launch_dense_f64(d, b, h->phases, h->bins, h->tune, s), "dense kernel launch");
     LCK(mark(5), "cudaEventRecord");
     LCK(launch_finish(d, b, h->tune.group, split ? 1 : 0, h->dd, lnL, dh, hh, s),
         "finish kernel launch");
     LCK(mark(6), "cudaEventRecord");
-    h->last_launches = split ? 7 : 6;  // band + knot kernels, splines, [segments], plan, dense, finish
+    h->last_launches = 7;  // band + knot kernels, splines, segments, plan, dense, finish
     return LISA_OK;
 }
 

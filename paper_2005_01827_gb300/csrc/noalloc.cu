@@ -38,7 +38,8 @@ void *g_addr[kMaxDevices] = {nullptr};
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t valid, tc, xpk, band, fedge, fk, kb, vals, mscr, coef, wrange, order, slot, grange, items,
+    size_t valid, tc, xpk, band, fedge, fk, kb, vals, mscr, coef, phases, wrange, order, slot,
+        grange, items,
         counter, err, part, end;
 };
 
@@ -60,6 +61,7 @@ Layout layout_for(size_t B, size_t L, size_t K, size_t items) {
     o.vals = take(sizeof(double) * B * L * kNSeries * K);
     o.mscr = take(sizeof(double) * B * L * kScratchRows * K);
     o.coef = take(sizeof(double) * B * L * (K - 1) * 32);
+    o.phases = take(sizeof(unsigned long long) * B * L * (K - 1) * 4);
     o.wrange = take(sizeof(int) * 2 * B);
     o.order = take(sizeof(int) * B);
     o.slot = take(sizeof(int) * B);
@@ -185,7 +187,10 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
     if ((e = launch_spline(d, b, s)) != cudaSuccess) return cuda_error(e, "spline kernel launch");
     if ((e = launch_plan(d, b, kTile, tune.group, s)) != cudaSuccess)
         return cuda_error(e, "plan kernel launch");
-    if ((e = launch_dense_f64(d, b, d_bins, tune, s)) != cudaSuccess)
+    unsigned long long *phases = reinterpret_cast<unsigned long long *>(s8 + o.phases);
+    if ((e = launch_phaseprep(d, b, phases, s)) != cudaSuccess)
+        return cuda_error(e, "segment kernel launch");
+    if ((e = launch_dense_f64(d, b, phases, d_bins, tune, s)) != cudaSuccess)
         return cuda_error(e, "dense kernel launch");
     if ((e = launch_finish(d, b, tune.group, 0, dd, d_lnL, d_dh, d_hh, s)) != cudaSuccess)
         return cuda_error(e, "finish kernel launch");

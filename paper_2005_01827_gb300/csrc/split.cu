@@ -68,7 +68,9 @@ cudaError_t launch_prep_split(const double *bins, int N, float *out, cudaStream_
 // One thread per (walker, mode, segment): FP32 cubics of A 2^64 and the six transfer
 // components in t = (j - kb_s) / W_s over the segment's W_s bins, and the fixed-point
 // forward differences of the full phase at its first bin.
-__global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, SegRec *segs) {
+template <bool kFull>
+__global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, SegRec *segs,
+                                                      unsigned long long *phases) {
     const int K = d.K;
     const long long total = (long long)d.B * d.L * (K - 1);
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
         SegRec r;
         int slot = 0;
         for (int q = 0; q < kNSeries; q++) {
+            if (!kFull && q != 1) continue;
             const double c0 = cf[4 * q], c1 = cf[4 * q + 1], c2 = cf[4 * q + 2], c3 = cf[4 * q + 3];
             const double y = fma(a, fma(a, fma(a, c3, c2), c1), c0);
             const double y1 = fma(a, fma(3.0 * a, c3, 2.0 * c2), c1);
@@ -113,18 +116,32 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
             r.c[4 * slot + 3] = (float)(sc * c3 * wd * wd * wd);
             slot++;
         }
-        r.kb0 = kb0;
-        r.invw = 1.0f / (float)W;
-        r.pad0 = 0;
-        r.pad1 = 0;
-        segs[g] = r;
+        if (kFull) {
+            r.kb0 = kb0;
+            r.invw = 1.0f / (float)W;
+            r.pad0 = 0;
+            r.pad1 = 0;
+            segs[g] = r;
+        } else {
+            ulonglong2 *o = reinterpret_cast<ulonglong2 *>(phases + 4 * g);
+            o[0] = make_ulonglong2(r.p[0], r.p[1]);
+            o[1] = make_ulonglong2(r.p[2], r.p[3]);
+        }
     }
 }
 
 cudaError_t launch_segprep(const StageDims &d, const StageBufs &b, SegRec *segs, cudaStream_t s) {
     const long long total = (long long)d.B * d.L * (d.K - 1);
     const int blocks = (int)min((total + 255) / 256, (long long)152 * 32);
-    segprep_kernel<<<blocks, 256, 0, s>>>(d, b, segs);
+    segprep_kernel<true><<<blocks, 256, 0, s>>>(d, b, segs, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phaseprep(const StageDims &d, const StageBufs &b, unsigned long long *phases,
+                             cudaStream_t s) {
+    const long long total = (long long)d.B * d.L * (d.K - 1);
+    const int blocks = (int)min((total + 255) / 256, (long long)152 * 32);
+    segprep_kernel<false><<<blocks, 256, 0, s>>>(d, b, nullptr, phases);
     return cudaGetLastError();
 }
 
