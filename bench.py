@@ -49,6 +49,10 @@ FLOP_BIN = 29
 # data bytes streamed per bin by a walker tile (w and w*d for A, E, T, FP64) and the
 # spline coefficients per segment (8 series x 4 doubles)
 BYTES_BIN = 72
+# DRAM bytes per (walker, bin) of dense_f64_kernel<8, 8> from one ncu capture of 32
+# walkers (dram__bytes_read.sum + dram__bytes_write.sum = 751.3 MB over 69,589,136
+# walker-bins); scaled to a launch by its walker-bins.  None once the kernel changes.
+TRAFFIC_F64_PER_WALKER_BIN = 751.3e6 / 69589136
 
 
 def peaks():
@@ -129,6 +133,8 @@ class ClockSampler:
 
 
 def dist_init():
+    """Rank layout from torchrun's environment; NCCL between GPUs (gloo when
+    BENCH_BACKEND=gloo, used by the CPU tests of this logic)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -137,6 +143,16 @@ def dist_init():
 
         dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
     return world, rank, local
+
+
+def walker_seed(c3: bool, rank: int) -> int:
+    """Each rank evaluates its own walkers (replicas, weak scaling): distinct seeds."""
+    return (3 if c3 else 1) + 1000 * rank
+
+
+def job_value(world: int, walkers_per_rank: int, steps: int, ms_max: float) -> float:
+    """Evaluations per second of the whole job: all ranks' walkers over the slowest rank."""
+    return world * walkers_per_rank * steps / (ms_max * 1e-3)
 
 
 def barrier(world):
@@ -152,7 +168,8 @@ def max_over_ranks(world, x):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -289,7 +306,7 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    return {"value": world * B * args.steps / (ms * 1e-3), "unit": "evals/s",
+    return {"value": job_value(world, B, args.steps, ms), "unit": "evals/s",
             "ms_per_step": ms / args.steps, "dtype": "f32+f64", "graphs": graphs,
             "tile": {"bins_per_thread": shape[0], "group": shape[1], "blocks": shape[2]},
             "roofline": {"bound": "alu", "kernel": "dense_split_kernel", "achieved": achieved,
@@ -340,7 +357,7 @@ def main():
     B = 8192 if c3 and args.walkers == 1024 else args.walkers
     g = W.GRID_C2
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B, device=local)
-    th = make_inputs(lisalike, like, g, (3 if c3 else 1) + 1000 * rank, B,
+    th = make_inputs(lisalike, like, g, walker_seed(c3, rank), B,
                      (3.0, 9.0) if c3 else (5.0, 7.0))
     mode_bins, bins = work_units(like, th)
     if c3:
@@ -388,7 +405,7 @@ def main():
         lisalike.lisa_like_set_profiling(like.h, False)
     shape = lisalike.lisa_like_get_tune(like.h)
     ms = max_over_ranks(world, ms_local)
-    value = world * B * args.steps / (ms * 1e-3)
+    value = job_value(world, B, args.steps, ms)
     assert np.all(np.isfinite(lnL.cpu().numpy())), "non-finite ln L"
 
     # end to end through the host-pointer entry point: H2D of the parameters and D2H of
@@ -409,8 +426,10 @@ def main():
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
+    traffic = TRAFFIC_F64_PER_WALKER_BIN * bins if shape[:2] == (8, 8) else None
     roofline = {"bound": "alu", "kernel": "dense_f64_kernel", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch",
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "units_per_launch": {"walker_mode_bins": mode_bins, "walker_bins": bins},
                 "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
