@@ -53,6 +53,8 @@ struct Phase64 {
 };
 
 // fixed-point forward differences of a segment's phase moved to bin n of the segment
+// (Newton's forward-difference formula in modular arithmetic; for n > 0 the low words
+// add the carries of the 128-bit products)
 __device__ __forceinline__ Phase64 phase64_at(const unsigned long long *__restrict__ r, int n) {
     const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(r));
     const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(r) + 1);
@@ -65,6 +67,13 @@ __device__ __forceinline__ Phase64 phase64_at(const unsigned long long *__restri
     p.d1 = a.y + c1 * b.x + c2 * b.y;
     p.d2 = b.x + c1 * b.y;
     p.d3 = b.y;
+    if (n > 0) {
+        const ulonglong2 c = __ldg(reinterpret_cast<const ulonglong2 *>(r) + 2);
+        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2 *>(r) + 3);
+        p.ph += __umul64hi(c1, c.x) + __umul64hi(c2, c.y) + __umul64hi(c3, e.x);
+        p.d1 += __umul64hi(c1, c.y) + __umul64hi(c2, e.x);
+        p.d2 += __umul64hi(c1, e.x);
+    }
     return p;
 }
 
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
                     const int s = segment_of(kbm, K, jj);
                     seg[mi] = s;
                     knext[mi] = (s < K - 2) ? __ldg(kbm + s + 1) : 0x7fffffff;
-                    ph[mi] = phase64_at(segs + 4 * (wm * (K - 1) + s), jj - __ldg(kbm + s));
+                    ph[mi] = phase64_at(segs + kPhaseWords * (wm * (K - 1) + s), jj - __ldg(kbm + s));
                 }
             }
             double dh = 0.0, hh = 0.0;
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(128) dense_f64_kernel(StageDims d, StageBufs b
                         while (s < K - 2 && j >= __ldg(kbm + s + 1)) s++;
                         seg[mi] = s;
                         knext[mi] = (s < K - 2) ? __ldg(kbm + s + 1) : 0x7fffffff;
-                        ph[mi] = phase64_at(segs + 4 * (wm * (K - 1) + s), j - __ldg(kbm + s));
+                        ph[mi] = phase64_at(segs + kPhaseWords * (wm * (K - 1) + s), j - __ldg(kbm + s));
                     }
                     const int s = seg[mi];
                     const double x = f - __ldg(b.fk + wm * K + s);

@@ -59,8 +59,14 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, int group,
                         cudaStream_t s);
-// FP64 path: per segment, the full phase and its first three forward differences at the
-// segment's first bin as 64-bit fixed-point fractions of a turn ([B][L][K-1][4]).
+// Fixed-point phase record of one spline segment (kPhaseWords words): the full phase
+// phi - 2 pi f t_coal and its first three forward differences over one bin at the
+// segment's first bin, as fractions of a turn scaled by 2^64 (words 0..3), and the next
+// 64 fractional bits of the three differences (words 4..6), which keep anchors deep
+// inside long segments exact to the FP64 value of the differences; word 7 is padding.
+constexpr int kPhaseWords = 8;
+
+// FP64 path: the phase records of all segments ([B][L][K-1][kPhaseWords]).
 cudaError_t launch_phaseprep(const StageDims &d, const StageBufs &b, unsigned long long *phases,
                              cudaStream_t s);
 cudaError_t launch_dense_f64(const StageDims &d, const StageBufs &b,

@@ -47,7 +47,7 @@ struct lisa_like {
     double *bins = nullptr;   // [N][9] FP64 staged data
     float *bins32 = nullptr;  // [N][9] FP32 whitened data (split precision)
     SegRec *segs = nullptr;   // [max_batch][L][K-1] split-precision segment records
-    unsigned long long *phases = nullptr;  // [max_batch][L][K-1][4] FP64-path phase anchors
+    unsigned long long *phases = nullptr;  // [max_batch][L][K-1][8] FP64-path phase records
 
     // per-call buffers
     double *params = nullptr, *tc = nullptr, *xpk = nullptr, *fedge = nullptr, *fk = nullptr;
@@ -149,7 +149,7 @@ lisa_status alloc_batch(lisa_like_t *h) {
     if (h->precision == LISA_PREC_SPLIT)
         LCK(dalloc(&h->segs, B * L * (K - 1)), "device allocation (split segments)");
     else
-        LCK(dalloc(&h->phases, B * L * (K - 1) * 4), "device allocation (phase anchors)");
+        LCK(dalloc(&h->phases, B * L * (K - 1) * kPhaseWords), "device allocation (phase anchors)");
     LCK(cudaMallocHost(&h->h_params, sizeof(double) * B * kNPar), "pinned allocation");
     LCK(cudaMallocHost(&h->h_out, sizeof(double) * 3 * B), "pinned allocation");
     LCK(cudaMallocHost(&h->h_err, sizeof(int)), "pinned allocation");

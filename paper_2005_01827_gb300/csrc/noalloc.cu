@@ -61,7 +61,10 @@ Layout layout_for(size_t B, size_t L, size_t K, size_t items) {
     o.vals = take(sizeof(double) * B * L * kNSeries * K);
     o.mscr = take(sizeof(double) * B * L * kScratchRows * K);
     o.coef = take(sizeof(double) * B * L * (K - 1) * 32);
-    o.phases = take(sizeof(unsigned long long) * B * L * (K - 1) * 4);
+    // the knot values are dead once the splines exist: the phase records reuse them
+    o.phases = o.vals;
+    static_assert(sizeof(unsigned long long) * kPhaseWords <= sizeof(double) * kNSeries,
+                  "phase records fit in the knot-value rows");
     o.wrange = take(sizeof(int) * 2 * B);
     o.order = take(sizeof(int) * B);
     o.slot = take(sizeof(int) * B);

@@ -24,8 +24,10 @@ constexpr double kInvTwoPi = 0.15915494309189535;
 constexpr double kAmpScale = 18446744073709551616.0;    // 2^64: keeps A in FP32 range
 }  // namespace
 
-// fraction of a turn of x radians as a 64-bit two's-complement fixed-point number
-__device__ __forceinline__ unsigned long long turns_fixed(double x) {
+// fraction of a turn of x radians as a 128-bit two's-complement fixed-point number:
+// hi holds the turns scaled by 2^64 (modulo 2^64), lo the next 64 fractional bits
+__device__ __forceinline__ void turns_fixed(double x, unsigned long long &hi,
+                                            unsigned long long &lo) {
     const double k = rint(x * kInvTwoPi);
     double r = fma(-k, kTwoPiHi, x);
     r = fma(-k, kTwoPiMid, r);
@@ -33,7 +35,10 @@ __device__ __forceinline__ unsigned long long turns_fixed(double x) {
     double fr = r * kInvTwoPi;  // in about [-0.5, 0.5]
     if (fr >= 0.5) fr -= 1.0;
     if (fr < -0.5) fr += 1.0;
-    return (unsigned long long)__double2ll_rn(ldexp(fr, 64));
+    const double t = ldexp(fr, 64);  // exact scaling
+    const double ft = floor(t);      // exact
+    hi = (unsigned long long)(long long)ft;
+    lo = (unsigned long long)ldexp(t - ft, 64);  // t - ft in [0, 1), exact
 }
 
 __device__ __forceinline__ double bin_freq_s(double f0, double df, int j) {
@@ -103,10 +108,12 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
                 const double p1 = (y1 - tw) * d.df;
                 const double p2 = y2 * d.df * d.df;
                 const double p3 = c3 * d.df * d.df * d.df;
-                r.p[0] = turns_fixed(p0);
-                r.p[1] = turns_fixed(p1 + p2 + p3);
-                r.p[2] = turns_fixed(2.0 * p2 + 6.0 * p3);
-                r.p[3] = turns_fixed(6.0 * p3);
+                unsigned long long dummy;
+                turns_fixed(p0, r.ph[0], dummy);
+                turns_fixed(p1 + p2 + p3, r.ph[1], r.ph[4]);
+                turns_fixed(2.0 * p2 + 6.0 * p3, r.ph[2], r.ph[5]);
+                turns_fixed(6.0 * p3, r.ph[3], r.ph[6]);
+                r.ph[7] = 0;
                 continue;
             }
             const double sc = (q == 0) ? kAmpScale : 1.0;
@@ -119,13 +126,12 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
         if (kFull) {
             r.kb0 = kb0;
             r.invw = 1.0f / (float)W;
-            r.pad0 = 0;
-            r.pad1 = 0;
+            r.pad[0] = r.pad[1] = 0;
             segs[g] = r;
         } else {
-            ulonglong2 *o = reinterpret_cast<ulonglong2 *>(phases + 4 * g);
-            o[0] = make_ulonglong2(r.p[0], r.p[1]);
-            o[1] = make_ulonglong2(r.p[2], r.p[3]);
+            ulonglong2 *o = reinterpret_cast<ulonglong2 *>(phases + (size_t)kPhaseWords * g);
+            for (int q = 0; q < kPhaseWords / 2; q++)
+                o[q] = make_ulonglong2(r.ph[2 * q], r.ph[2 * q + 1]);
         }
     }
 }
@@ -162,8 +168,11 @@ struct PhaseState {
 };
 
 // forward differences of the segment's phase moved from its first bin to bin n
-// (Newton's forward-difference formula, exact in modular integer arithmetic)
-__device__ __forceinline__ PhaseState phase_at(const SegRec &r, int n) {
+// (Newton's forward-difference formula, exact in modular integer arithmetic; for n >= 0
+// the low words add the carries of the 128-bit products)
+__device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, int n) {
+    const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(rp->ph);
+    const ulonglong2 a = __ldg(w), b = __ldg(w + 1);
     const long long nn = n;
     const unsigned long long c1 = (unsigned long long)nn;
     // n(n-1) >= 0 and even; n(n-1)(n-2)/2 is a multiple of 3, so multiplying by the
@@ -171,11 +180,40 @@ __device__ __forceinline__ PhaseState phase_at(const SegRec &r, int n) {
     const unsigned long long c2 = (unsigned long long)(nn * (nn - 1)) >> 1;
     const unsigned long long c3 = (c2 * (unsigned long long)(nn - 2)) * 0xAAAAAAAAAAAAAAABull;
     PhaseState p;
-    p.ph = r.p[0] + c1 * r.p[1] + c2 * r.p[2] + c3 * r.p[3];
-    p.d1 = r.p[1] + c1 * r.p[2] + c2 * r.p[3];
-    p.d2 = r.p[2] + c1 * r.p[3];
-    p.d3 = r.p[3];
+    p.ph = a.x + c1 * a.y + c2 * b.x + c3 * b.y;
+    p.d1 = a.y + c1 * b.x + c2 * b.y;
+    p.d2 = b.x + c1 * b.y;
+    p.d3 = b.y;
+    if (n > 0) {
+        const ulonglong2 c = __ldg(w + 2), e = __ldg(w + 3);
+        p.ph += __umul64hi(c1, c.x) + __umul64hi(c2, c.y) + __umul64hi(c3, e.x);
+        p.d1 += __umul64hi(c1, c.y) + __umul64hi(c2, e.x);
+        p.d2 += __umul64hi(c1, e.x);
+    }
     return p;
+}
+
+// the FP32 cubic coefficients, first bin and 1/width of a segment record
+struct SegCoef {
+    float c[28];
+    int kb0;
+    float invw;
+};
+
+__device__ __forceinline__ SegCoef seg_coef(const SegRec *__restrict__ rp) {
+    SegCoef r;
+    const float4 *v = reinterpret_cast<const float4 *>(rp->c);
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+        const float4 x = __ldg(v + q);
+        r.c[4 * q] = x.x;
+        r.c[4 * q + 1] = x.y;
+        r.c[4 * q + 2] = x.z;
+        r.c[4 * q + 3] = x.w;
+    }
+    r.kb0 = __ldg(&rp->kb0);
+    r.invw = __ldg(&rp->invw);
+    return r;
 }
 
 // e^{2 pi i ph / 2^64}: table entry of the top 8 bits times a short polynomial in the
@@ -225,7 +263,7 @@ __device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
 }
 
 template <int C, int G>
-__global__ void __launch_bounds__(128) dense_split_kernel(StageDims d, StageBufs b,
+__global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageBufs b,
                                                           const SegRec *__restrict__ segs,
                                                           const float *__restrict__ bins,
                                                           int tile_bins) {
@@ -329,9 +367,9 @@ __global__ void __launch_bounds__(128) dense_split_kernel(StageDims d, StageBufs
                 const int *kb = b.kb + wm * K;
                 const SegRec *sg = segs + wm * (K - 1);
                 int s = seg_guess(kb, K, ja, fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
-                SegRec r = sg[s];
+                SegCoef r = seg_coef(sg + s);
                 int knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
-                PhaseState p = phase_at(r, ja - r.kb0);
+                PhaseState p = phase_at(sg + s, ja - r.kb0);
                 float t = (float)(ja - r.kb0) * r.invw;
                 if (ja == j0 && jb == j0 + C && knext >= j0 + C) {
                     // the whole chunk lies in one segment and in the band: no predicates
@@ -366,9 +404,9 @@ __global__ void __launch_bounds__(128) dense_split_kernel(StageDims d, StageBufs
                     if (j < ja || j >= jb) continue;
                     if (j >= knext) {  // the chunk crosses into the next segment
                         s++;
-                        r = sg[s];
+                        r = seg_coef(sg + s);
                         knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
-                        p = phase_at(r, j - r.kb0);
+                        p = phase_at(sg + s, j - r.kb0);
                         t = (float)(j - r.kb0) * r.invw;
                     }
                     float v[7];

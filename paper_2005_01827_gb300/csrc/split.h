@@ -10,19 +10,18 @@ namespace lisa {
 // (re, im); 36 bytes.
 constexpr int kBinFloats = 9;
 
-// One spline segment of one (walker, mode) in the split-precision form, 160 bytes:
+// One spline segment of one (walker, mode) in the split-precision form, 192 bytes:
 // c[4 q + k] is the t^k coefficient (t = (j - kb0) / W over the segment's W bins) of
-// series q = A 2^64, Re T^A, Im T^A, Re T^E, Im T^E, Re T^T, Im T^T; p[] holds the full
-// phase and its first three forward differences at bin kb0 as fractions of a turn
-// scaled by 2^64.
+// series q = A 2^64, Re T^A, Im T^A, Re T^E, Im T^E, Re T^T, Im T^T; ph[] is the
+// fixed-point phase record of the segment (see kernels.h).
 struct __align__(16) SegRec {
     float c[28];
-    unsigned long long p[4];
+    unsigned long long ph[kPhaseWords];
     int kb0;
     float invw;
-    int pad0, pad1;
+    int pad[2];
 };
-static_assert(sizeof(SegRec) == 160, "segment record is 160 bytes");
+static_assert(sizeof(SegRec) == 192, "segment record is 192 bytes");
 
 cudaError_t launch_prep_split(const double *bins, int N, float *out, cudaStream_t s);
 cudaError_t launch_segprep(const StageDims &d, const StageBufs &b, SegRec *segs, cudaStream_t s);

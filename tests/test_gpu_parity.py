@@ -183,6 +183,33 @@ def test_edge_cases(pkg, orc):
         like.close()
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_phase_stays_exact_along_long_segments(pkg, orc, split):
+    """With d = i h, <d|h> vanishes in exact arithmetic and is first order in any phase
+    error of the dense evaluation; K = 16 knots over the 1-yr grid makes segments of
+    ~1e6 bins, so a phase recurrence that drifts along a segment shows up here."""
+    g = W.GRID_C2
+    th = W.theta_table2(1)
+    th[0] = 1e5                       # band reaching the top of the grid
+    K = 16
+    S = orc.psd_aet(g.freqs())
+    h = orc.template(th, W.T0_YEAR, [(2, 2)], K, g.f0, g.df, g.n_bins)
+    like = pkg.LisaLike(modes=[(2, 2)], n_knots=K, max_batch=1,
+                        precision=pkg.LISA_PREC_SPLIT if split else pkg.LISA_PREC_FP64)
+    like.set_data(g.f0, g.df, g.n_bins, 1j * h, S)
+    band, _, fk, _ = like.stage_knots(th)
+    widest = np.max(np.diff(fk[0, 0])) / g.df
+    assert widest > 5e5
+    lnL, dh, hh = like.loglike(th)
+    like.close()
+    # FP64 resolves a phase of ~1e7 rad to ~2e-9 rad (the oracle's own per-bin rounding);
+    # a recurrence drifting along these segments would give O(1e-1)
+    tol = 1e-6 if split else 1e-8
+    print("long segments (%.0f bins): |<i h|h>| / <h|h> = %.2e" % (widest, abs(dh[0]) / hh[0]))
+    assert abs(dh[0]) <= tol * hh[0]
+    assert abs(hh[0] / orc.inner(h, h, S, g.df) - 1) <= (1e-6 if split else 1e-10)
+
+
 def test_errors_and_state(pkg, orc):
     from paper_2005_01827_gb300 import lisalike as LL
 
