@@ -276,8 +276,7 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B,
                     device=torch.cuda.current_device(), precision=lisalike.LISA_PREC_SPLIT)
     make_inputs(lisalike, like, g, 1, 1)          # same data as the FP64 handle
-    if graphs:
-        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
     dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
     lnL = torch.empty(B, dtype=torch.float64, device="cuda")
 
@@ -360,8 +359,8 @@ def main():
     th = make_inputs(lisalike, like, g, walker_seed(c3, rank), B,
                      (3.0, 9.0) if c3 else (5.0, 7.0))
     mode_bins, bins = work_units(like, th)
-    if c3:
-        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    # tile shapes from the autotuner (timed on a 256-walker sample of the workload)
+    lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
 
     # a dedicated stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()

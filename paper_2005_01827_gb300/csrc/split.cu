@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
     __shared__ float2 tab[256];
     __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
     __shared__ float s_flo[G][kMaxModes], s_scl[G][kMaxModes];
-    __shared__ double red[2][4];
+    __shared__ double red[G][2][4];  // per slot, per warp partial sums
+    __shared__ int s_skip[G];
     const int tid = threadIdx.x;
     for (int k = tid; k < 256; k += blockDim.x) {
         double sn, cs;
@@ -341,15 +342,11 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
 
         for (int k = 0; k < G; k++) {
             const int w = s_walker[k];
-            if (w < 0) continue;
-            const size_t slot = (size_t)item * G + k;
-            if (b.wrange[2 * w + 1] < J0 || b.wrange[2 * w] >= Jend) {
-                if (tid == 0) {
-                    b.part[2 * slot] = 0.0;
-                    b.part[2 * slot + 1] = 0.0;
-                }
+            if (w < 0 || b.wrange[2 * w + 1] < J0 || b.wrange[2 * w] >= Jend) {
+                if (tid == 0) s_skip[k] = 1;  // empty slot or band outside the tile
                 continue;
             }
+            if (tid == 0) s_skip[k] = 0;
             const int j0 = J0 + tid * C;
             float hr[C][3], hm[C][3];
 #pragma unroll
@@ -463,20 +460,22 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
             warp_sum_pair(rs, rl);
             warp_sum_pair(hs, hl);
             if ((tid & 31) == 0) {
-                red[0][tid >> 5] = (double)rs + (double)rl;
-                red[1][tid >> 5] = (double)hs + (double)hl;
+                red[k][0][tid >> 5] = (double)rs + (double)rl;
+                red[k][1][tid >> 5] = (double)hs + (double)hl;
             }
-            __syncthreads();
-            if (tid == 0) {
-                double a = 0.0, c = 0.0;
+        }
+        // one block barrier per item: thread k sums slot k over the warps
+        __syncthreads();
+        if (tid < G && s_walker[tid] >= 0) {
+            const size_t slot = (size_t)item * G + tid;
+            double a = 0.0, c = 0.0;
+            if (!s_skip[tid])
                 for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
-                    a += red[0][q];
-                    c += red[1][q];
+                    a += red[tid][0][q];
+                    c += red[tid][1][q];
                 }
-                b.part[2 * slot] = a;
-                b.part[2 * slot + 1] = c;
-            }
-            __syncthreads();
+            b.part[2 * slot] = a;
+            b.part[2 * slot + 1] = c;
         }
     }
 }
