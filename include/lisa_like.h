@@ -192,6 +192,14 @@ lisa_status lisa_like_get_tune(const lisa_like_t *h, int *out);
  * Requires set_data. */
 lisa_status lisa_like_autotune(lisa_like_t *h, const double *params, int B, int *out);
 
+/* Per-mode inner products, each mode's template alone (no cross terms): for walker b
+ * and mode i (the config's order), dh_modes[b][i] = <d|h_i> and hh_modes[b][i] =
+ * <h_i|h_i>, the per-harmonic SNR^2 of Table III computed "in isolation".  Because
+ * the template is a sum over modes, sum_i <d|h_i> = <d|h> of loglike.  Host buffers
+ * double[B][n_modes] (either may be NULL); blocks until done. */
+lisa_status lisa_like_mode_inner(lisa_like_t *h, const double *params, int B, double *dh_modes,
+                                 double *hh_modes);
+
 /* Number of kernel launches the last loglike / loglike_device call enqueued. */
 int lisa_like_last_launches(const lisa_like_t *h);
 

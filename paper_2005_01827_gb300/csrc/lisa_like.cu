@@ -243,7 +243,7 @@ bool make_tune(const lisa_like_t *h, int per_thread, int group, DenseTune *t) {
 }
 
 lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
-                    double *hh, cudaStream_t s, bool profile);
+                    double *hh, cudaStream_t s, bool profile, int only_mode = -1);
 
 void drop_graph(lisa_like_t *h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -291,8 +291,9 @@ lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     return LISA_OK;
 }
 
+// the call's kernels on stream s; only_mode >= 0 restricts the template to that one mode
 lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
-                    double *hh, cudaStream_t s, bool profile) {
+                    double *hh, cudaStream_t s, bool profile, int only_mode) {
     cudaEvent_t *ev = nullptr;
     if (profile) {
         if (h->prof_calls >= 4096) return fail(h, LISA_ERR_STATE, "read the profile first");
@@ -301,7 +302,12 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
         h->prof_calls++;
     }
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
-    const StageDims d = dims_of(h, B);
+    StageDims d = dims_of(h, B);
+    if (only_mode >= 0) {
+        d.L = 1;
+        d.ml[0] = h->ml[only_mode];
+        d.mm[0] = h->mm[only_mode];
+    }
     const StageBufs b = bufs_of(h, dparams);
     const int tile = h->tune.threads * h->tune.per_thread;
     const bool split = h->precision == LISA_PREC_SPLIT;
@@ -784,6 +790,38 @@ lisa_status lisa_like_autotune(lisa_like_t *h, const double *params, int B, int 
         out[1] = h->tune.group;
         out[2] = h->tune.blocks;
     }
+    return LISA_OK;
+}
+
+lisa_status lisa_like_mode_inner(lisa_like_t *h, const double *params, int B, double *dh_modes,
+                                 double *hh_modes) {
+    if (!h) return LISA_ERR_ARG;
+    if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
+    if (B < 1 || B > h->max_batch || !params || (!dh_modes && !hh_modes))
+        return fail(h, LISA_ERR_ARG, "bad batch or NULL outputs");
+    LCK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = h->stream;
+    LCK(cudaMemcpyAsync(h->params, params, sizeof(double) * kNPar * B, cudaMemcpyHostToDevice, s),
+        "parameter upload");
+    const int L = h->L;
+    std::vector<double> buf((size_t)2 * B * L);
+    for (int mi = 0; mi < L; mi++) {
+        lisa_status st = enqueue(h, h->params, B, h->out, h->out + B, h->out + 2 * B, s, false, mi);
+        if (st != LISA_OK) return st;
+        LCK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s),
+            "result download");
+        LCK(cudaMemcpyAsync(h->h_err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s),
+            "result download");
+        st = wait_for(h, s);
+        if (st != LISA_OK) return st;
+        if (*h->h_err) return fail(h, LISA_ERR_TIMEOUT, "a device wait for staged data gave up");
+        for (int b = 0; b < B; b++) {
+            buf[(size_t)b * L + mi] = h->h_out[B + b];
+            buf[(size_t)B * L + (size_t)b * L + mi] = h->h_out[2 * B + b];
+        }
+    }
+    if (dh_modes) std::memcpy(dh_modes, buf.data(), sizeof(double) * B * L);
+    if (hh_modes) std::memcpy(hh_modes, buf.data() + (size_t)B * L, sizeof(double) * B * L);
     return LISA_OK;
 }
 

@@ -30,6 +30,7 @@ SYMBOLS = (
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
     "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
+    "lisa_like_mode_inner",
 )
 NOALLOC_SCRATCH_BYTES = 4194304
 NOALLOC_MAX_WALKER_MODE_KNOTS = 8192
@@ -107,6 +108,8 @@ def load(path: str = LIB_PATH):
     L.lisa_like_get_tune.restype = i
     L.lisa_like_autotune.argtypes = [vp, vp, i, ip]
     L.lisa_like_autotune.restype = i
+    L.lisa_like_mode_inner.argtypes = [vp, vp, i, vp, vp]
+    L.lisa_like_mode_inner.restype = i
     L.lisa_like_last_launches.argtypes = [vp]
     L.lisa_like_last_launches.restype = i
     L.lisa_like_destroy.argtypes = [vp]
@@ -235,6 +238,10 @@ def lisa_like_autotune(h, params, B):
     return tuple(out)
 
 
+def lisa_like_mode_inner(h, params, B, dh_modes=None, hh_modes=None):
+    _check(load().lisa_like_mode_inner(h, _ptr(params), B, _ptr(dh_modes), _ptr(hh_modes)), h)
+
+
 def lisa_like_last_launches(h) -> int:
     return load().lisa_like_last_launches(h)
 
@@ -318,6 +325,15 @@ class LisaLike:
         coef = np.empty((B, self.L, self.K - 1, 8, 4))
         lisa_like_stage_coeffs(self.h, p, B, coef)
         return coef
+
+    def mode_inner(self, params):
+        """Per-mode <d|h_i> and <h_i|h_i>, arrays [B, n_modes]."""
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        dh = np.empty((B, self.L))
+        hh = np.empty((B, self.L))
+        lisa_like_mode_inner(self.h, p, B, dh, hh)
+        return dh, hh
 
     def last_launches(self):
         return lisa_like_last_launches(self.h)
