@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lisa_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "oracle_sampler.c"))
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -33,13 +34,14 @@ NSERIES = 8
 
 def build(force: bool = False) -> str:
     """Compile lisa_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    deps = _SRCS + (os.path.join(_HERE, "oracle.h"),)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
+        os.path.getmtime(p) for p in deps
     ):
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.check_call(cmd, cwd=_HERE)
     os.replace(tmp, _LIB)
     return _LIB
@@ -84,8 +86,36 @@ def lib():
             L.oracle_dl_gpc.argtypes = [d]
             L.oracle_dl_gpc.restype = d
             L.oracle_polarizations.argtypes = [dp, d, i, i, dp, i64, dp, dp]
+            u32p = C.POINTER(C.c_uint32)
+            llp = C.POINTER(C.c_longlong)
+            cfgp = C.POINTER(SamplerCfg)
+            L.oracle_philox.argtypes = [u32p, u32p, u32p]
+            L.oracle_philox.restype = None
+            for fn in (L.oracle_lisa_to_ssb, L.oracle_ssb_to_lisa):
+                fn.argtypes = [dp, dp]
+                fn.restype = None
+            L.oracle_to_physical.argtypes = [dp, i, d, dp]
+            L.oracle_to_physical.restype = None
+            L.oracle_default_ladder.argtypes = [i, d, i, dp]
+            L.oracle_default_ladder.restype = None
+            L.oracle_adapt_ladder.argtypes = [i, dp, dp, d]
+            L.oracle_adapt_ladder.restype = None
+            L.oracle_sampler_gauss.argtypes = [cfgp, dp, dp, i, i, dp, dp, dp, dp, llp, llp]
+            L.oracle_sampler_lisa.argtypes = [cfgp, d, ip, i, i, d, d, i64, dp, dp, i, i, i, dp,
+                                              dp, dp, dp, llp, llp]
+            L.oracle_autocorr_time.argtypes = [dp, i, i, dp]
+            L.oracle_autocorr_time.restype = d
             _lib = L
     return _lib
+
+
+class SamplerCfg(C.Structure):
+    """Mirror of oracle_sampler_cfg."""
+    _fields_ = [("T", C.c_int), ("W", C.c_int), ("a", C.c_double),
+                ("betas", C.POINTER(C.c_double)), ("adaptive", C.c_int),
+                ("adapt_lag", C.c_double), ("adapt_time", C.c_double),
+                ("seed", C.c_uint64), ("lower", C.POINTER(C.c_double)),
+                ("upper", C.POINTER(C.c_double)), ("lisa_frame", C.c_int)]
 
 
 def _dp(a):
@@ -269,3 +299,127 @@ def polarizations(th, t0, l, m, f):
     if not lib().oracle_polarizations(_dp(_f64(th)), t0, l, m, _dp(f), f.size, _dp(hp), _dp(hc)):
         raise ValueError("invalid parameters or mode")
     return hp[:, 0] + 1j * hp[:, 1], hc[:, 0] + 1j * hc[:, 1]
+
+
+# --------------------------------------------------------------------------- sampler
+
+def philox(ctr, key):
+    """One Philox4x32-10 block (Salmon et al. 2011): four uint32 words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.empty(4, dtype=np.uint32)
+    u32p = C.POINTER(C.c_uint32)
+    lib().oracle_philox(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), o.ctypes.data_as(u32p))
+    return o
+
+
+def lisa_to_ssb(t, lam, beta, psi):
+    """LISA frame -> SSB frame: (t_L, lambda_L, beta_L, psi_L) -> (t, lambda, beta, psi)."""
+    o = np.empty(4)
+    lib().oracle_lisa_to_ssb(_dp(_f64([t, lam, beta, psi])), _dp(o))
+    return tuple(o)
+
+
+def ssb_to_lisa(t, lam, beta, psi):
+    o = np.empty(4)
+    lib().oracle_ssb_to_lisa(_dp(_f64([t, lam, beta, psi])), _dp(o))
+    return tuple(o)
+
+
+def from_physical(th):
+    """Sampling coordinates of Table I from physical parameters (SSB frame)."""
+    th = _f64(th)
+    return np.array([np.log(th[0]), th[1], th[2], th[3], np.log(th[4]), th[5], np.cos(th[6]),
+                     th[7], np.sin(th[8]), th[9], np.log(th[10])])
+
+
+def to_physical(x, lisa_frame=False, t0=0.0):
+    """Physical parameters from the sampling coordinates of Table I."""
+    x = _f64(x)
+    th = np.empty(NPAR)
+    lib().oracle_to_physical(_dp(x), int(lisa_frame), float(t0), _dp(th))
+    return th
+
+
+def default_ladder(T, ratio=2.04807, t_max_inf=True):
+    b = np.empty(T)
+    lib().oracle_default_ladder(int(T), float(ratio), int(t_max_inf), _dp(b))
+    return b
+
+
+def adapt_ladder(betas, A, kappa):
+    b = _f64(betas).copy()
+    lib().oracle_adapt_ladder(b.size, _dp(b), _dp(_f64(A)), float(kappa))
+    return b
+
+
+class SamplerRun:
+    """Result of an oracle sampler run: final state, cold chain, counters, ladder."""
+
+    def __init__(self, x, lnl, chain, lnl_chain, acc, swaps, betas):
+        self.x, self.lnl, self.chain, self.lnl_chain = x, lnl, chain, lnl_chain
+        self.acc, self.swaps, self.betas = acc, swaps, betas
+
+
+def _sampler_cfg(x, betas, a, seed, lower, upper, adaptive, adapt_lag, adapt_time, lisa_frame):
+    T, W = x.shape[0], x.shape[1]
+    keep = dict(betas=_f64(betas).copy(), lo=_f64(lower), hi=_f64(upper))
+    cfg = SamplerCfg(T=T, W=W, a=float(a), betas=_dp(keep["betas"]), adaptive=int(adaptive),
+                     adapt_lag=float(adapt_lag), adapt_time=float(adapt_time), seed=int(seed),
+                     lower=_dp(keep["lo"]), upper=_dp(keep["hi"]), lisa_frame=int(lisa_frame))
+    return cfg, keep
+
+
+def _sampler_out(T, W, n_steps):
+    return (np.empty((n_steps, W, NPAR)), np.empty((n_steps, W)), np.zeros((T, 2), np.int64),
+            np.zeros((T, 2), np.int64), np.empty((T, W)))
+
+
+def sampler_gauss(x0, betas, mean, sigma, n_steps, seed, lower, upper, a=1.15, step0=0,
+                  adaptive=False, adapt_lag=10000.0, adapt_time=100.0):
+    """PT stretch sampler (Sec. III) on N(mean, diag(sigma^2)); x0 [T, W, 11]."""
+    x = _f64(x0).copy()
+    T, W = x.shape[0], x.shape[1]
+    cfg, keep = _sampler_cfg(x, betas, a, seed, lower, upper, adaptive, adapt_lag, adapt_time,
+                             False)
+    chain, lch, acc, sw, lnl = _sampler_out(T, W, n_steps)
+    llp = C.POINTER(C.c_longlong)
+    ok = lib().oracle_sampler_gauss(C.byref(cfg), _dp(_f64(mean)), _dp(_f64(sigma)), int(step0),
+                                    int(n_steps), _dp(x), _dp(lnl), _dp(chain), _dp(lch),
+                                    acc.ctypes.data_as(llp), sw.ctypes.data_as(llp))
+    if not ok:
+        raise ValueError("invalid sampler arguments")
+    return SamplerRun(x, lnl, chain, lch, acc, sw, keep["betas"])
+
+
+def sampler_lisa(x0, betas, n_steps, seed, lower, upper, t0, modes, K, f0, df, d, psd,
+                 a=1.15, step0=0, adaptive=False, adapt_lag=10000.0, adapt_time=100.0,
+                 lisa_frame=True, n_threads=None):
+    """PT stretch sampler (Sec. III) on the LISA likelihood of Eq. (2)."""
+    x = _f64(x0).copy()
+    T, W = x.shape[0], x.shape[1]
+    cfg, keep = _sampler_cfg(x, betas, a, seed, lower, upper, adaptive, adapt_lag, adapt_time,
+                             lisa_frame)
+    chain, lch, acc, sw, lnl = _sampler_out(T, W, n_steps)
+    md = _modes(modes)
+    d2, p = _cplx_pairs(d), _f64(psd)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    llp = C.POINTER(C.c_longlong)
+    ok = lib().oracle_sampler_lisa(C.byref(cfg), float(t0), md.ctypes.data_as(C.POINTER(C.c_int)),
+                                   len(md), int(K), float(f0), float(df), p.shape[-1], _dp(d2),
+                                   _dp(p), int(n_threads), int(step0), int(n_steps), _dp(x),
+                                   _dp(lnl), _dp(chain), _dp(lch), acc.ctypes.data_as(llp),
+                                   sw.ctypes.data_as(llp))
+    if not ok:
+        raise ValueError("invalid sampler arguments")
+    return SamplerRun(x, lnl, chain, lch, acc, sw, keep["betas"])
+
+
+def autocorr_time(series, return_rho=False):
+    """Sec. III.C estimator on series[n, W] (one parameter, every walker)."""
+    s = _f64(series)
+    n, W = s.shape
+    rho = np.empty(n)
+    tau = lib().oracle_autocorr_time(_dp(s), n, W, _dp(rho))
+    return (tau, rho) if return_rho else tau

@@ -107,6 +107,52 @@ double oracle_dl_gpc(double z);
 int oracle_polarizations(const double *th, double t0, int l, int m, const double *f, int64_t n,
                          double *hp, double *hc);
 
+/* ---------------------------------------------------------------- sampler (Sec. III) */
+
+/* Philox4x32-10 block: out = philox(ctr, key) */
+void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* LISA-frame <-> SSB-frame sky position, polarisation and arrival time (Sec. II);
+ * in/out = (t [s, absolute], lambda, beta, psi) */
+void oracle_lisa_to_ssb(const double *in, double *out);
+void oracle_ssb_to_lisa(const double *in, double *out);
+
+/* physical parameters (header order above) from the sampling coordinates of Table I:
+ * (ln M_T, q, a1, a2, ln D_L, phi_ref, cos iota, lambda, sin beta, psi, ln t_ref) */
+void oracle_to_physical(const double *x, int lisa_frame, double t0, double *th);
+
+/* geometric ladder beta_t = ratio^-t; the hottest beta = 0 when t_max_inf */
+void oracle_default_ladder(int T, double ratio, int t_max_inf, double *betas);
+/* one adaptive ladder update from the per-pair swap acceptances A[T-1] */
+void oracle_adapt_ladder(int T, double *betas, const double *A, double kappa);
+
+typedef struct {
+    int T, W;              /* temperatures; walkers per temperature (even, >= 4) */
+    double a;              /* stretch scale of Eq. (15) */
+    double *betas;         /* [T] inverse temperatures, updated by the adaptive ladder */
+    int adaptive;          /* Vousden et al. ladder adaptation */
+    double adapt_lag, adapt_time;
+    uint64_t seed;
+    const double *lower, *upper; /* [11] uniform prior box */
+    int lisa_frame;        /* lambda, beta, psi, t_ref sampled in the LISA frame */
+} oracle_sampler_cfg;
+
+/* n_steps of the PT stretch sampler on a Gaussian target (mean, sigma [11]) or on the
+ * LISA likelihood; x [T][W][11] and lnl [T][W] are the state in/out; chain
+ * [n_steps][W][11] and lnl_chain [n_steps][W] record the coldest temperature (may be
+ * NULL); acc and swaps [T][2] accumulate (accepted, proposed). */
+int oracle_sampler_gauss(const oracle_sampler_cfg *c, const double *mean, const double *sigma,
+                         int step0, int n_steps, double *x, double *lnl, double *chain,
+                         double *lnl_chain, long long *acc, long long *swaps);
+int oracle_sampler_lisa(const oracle_sampler_cfg *c, double t0, const int *modes, int n_modes,
+                        int K, double f0, double df, int64_t n_bins, const double *d,
+                        const double *psd, int n_threads, int step0, int n_steps, double *x,
+                        double *lnl, double *chain, double *lnl_chain, long long *acc,
+                        long long *swaps);
+
+/* autocorrelation time of Sec. III.C for chain[n][W]; rho_out [n] may be NULL */
+double oracle_autocorr_time(const double *chain, int n, int W, double *rho_out);
+
 #ifdef __cplusplus
 }
 #endif

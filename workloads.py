@@ -26,6 +26,19 @@ MODES6 = ((2, 2), (3, 3), (4, 4), (2, 1), (3, 2), (4, 3))
 YEAR_S = 3.15576e7
 DAY_S = 86400.0
 
+# Table I of the paper: uniform prior box of the sampling coordinates
+# (ln M_T, q, a1, a2, ln D_L [Gpc], phi_ref, cos iota, lambda, sin beta, psi, ln t_ref [s]).
+TABLE1_LOWER = np.array([math.log(1e3), 0.05, -0.99, -0.99, math.log(0.044), 0.0, -1.0, 0.0,
+                         -1.0, 0.0, math.log(1.0)])
+TABLE1_UPPER = np.array([math.log(1e9), 1.0, 0.99, 0.99, math.log(1298.0), 2 * math.pi, 1.0,
+                         2 * math.pi, 1.0, math.pi, math.log(3.15576e8)])
+
+# Parallel-tempered sampler workload: 8 temperatures x 256 walkers around an injection
+# with M_T = 2e6 Msun, q = 0.5, z = 3 (other parameters as Table II's Binary 1).
+SAMPLER_T, SAMPLER_W = 8, 256
+THETA_SAMPLER_Z = (2e6, 0.5, 0.0, 0.0, 3.0, 2.14, 1.05, -0.024 % (2 * math.pi), 0.62, 2.03,
+                   50.25)
+
 # Table II of the paper: Binary, M_T [Msun], q, a1, a2, D_L [Gpc], phi_ref, iota,
 # lambda, beta, psi, t_ref [s], SNR (the injections studied in Sec. IV).
 TABLE2 = {
