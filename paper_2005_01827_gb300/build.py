@@ -17,7 +17,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblisalike.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["lisa_like.cu", "stages.cu", "plan.cu", "dense.cu", "split.cu", "noalloc.cu"]
+SOURCES = ["lisa_like.cu", "stages.cu", "plan.cu", "dense.cu", "split.cu", "noalloc.cu",
+           "sampler.cu"]
 
 
 def nvcc() -> str:
@@ -32,7 +33,8 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(SRC, f) for f in os.listdir(SRC)]
-    deps.append(os.path.join(os.path.dirname(HERE), "include", "lisa_like.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc)]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

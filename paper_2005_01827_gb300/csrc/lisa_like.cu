@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/lisa_like.h"
+#include "internal.h"
 #include "kernels.h"
 #include "model.cuh"
 #include "split.h"
@@ -27,6 +28,7 @@ thread_local std::string g_create_error;
 namespace lisa {
 // failure text of handle-free entry points, read back by lisa_like_last_error(NULL)
 void set_thread_error(const std::string &msg) { g_create_error = msg; }
+const char *thread_error() { return g_create_error.c_str(); }
 }  // namespace lisa
 
 struct lisa_like {
@@ -336,6 +338,31 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
 }
 
 }  // namespace
+
+namespace lisa {
+
+LikeInfo like_info(const lisa_like_t *h) {
+    LikeInfo i;
+    i.stream = h->stream;
+    i.device = h->device;
+    i.max_batch = h->max_batch;
+    i.have_data = h->have_data ? 1 : 0;
+    i.t0 = h->t0;
+    i.err_flag = h->err_flag;
+    i.timeout_s = h->timeout_s;
+    return i;
+}
+
+lisa_status like_enqueue(lisa_like_t *h, const double *d_params, int B, double *d_lnL,
+                         cudaStream_t s, int *launches) {
+    if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
+    if (B < 1 || B > h->max_batch) return fail(h, LISA_ERR_ARG, "B must be in [1, max_batch]");
+    lisa_status st = enqueue(h, d_params, B, d_lnL, nullptr, nullptr, s, false);
+    if (launches) *launches = h->last_launches;
+    return st;
+}
+
+}  // namespace lisa
 
 extern "C" {
 

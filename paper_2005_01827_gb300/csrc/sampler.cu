@@ -1,0 +1,896 @@
+// sampler.cu -- the parallel-tempered affine-invariant ensemble sampler of Katz et al.
+// (2020), Sec. III, on the device: stretch proposals, tempered Metropolis-Hastings
+// acceptance, temperature swaps and the adaptive ladder as CUDA kernels around the
+// batched likelihood, one CUDA graph per step.  C ABI: include/lisa_sampler.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lisa_sampler.h"
+#include "internal.h"
+
+namespace {
+
+constexpr int D = LISA_SAMPLER_NDIM;
+constexpr int kMaxT = LISA_SAMPLER_MAX_TEMPS;
+constexpr int kThreads = 128;
+constexpr int kSwapThreads = 256;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kYearS = 3.15576e7;                  // orbital period of the constellation
+constexpr double kAuS = 1.495978707e11 / 299792458.0;  // 1 AU in light seconds
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror & Shaw (2011): ten rounds of two
+// 32x32 -> 64-bit products with the Weyl key schedule.
+__host__ __device__ inline uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+struct U4 {
+    uint32_t v[4];
+};
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; r++) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = mulhi32(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = mulhi32(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    U4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+// uniform in (0, 1): (u + 1/2) 2^-32, exact in FP64
+__host__ __device__ inline double unit(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
+
+// ------------------------------------------------------------------ device state
+struct RecCtl {
+    double *chain;  // [n][W][D] or NULL
+    double *lnl;    // [n][W] or NULL
+    int i;          // next row
+    int pad;
+};
+
+struct Dev {
+    int T, W, H, target, lisa_frame, adaptive;
+    uint32_t k0, k1;
+    double a, t0, lag, nu;
+    double lo[D], hi[D], mean[D], sig[D];
+    double *x, *lnl, *lnp, *betas;       // [T][W][D], [T][W], [T][W], [T]
+    double *y, *pth, *ly, *z, *py;       // [T*H][D], [T*H][D], [T*H] x3
+    unsigned long long *acc, *swaps;     // [T][2]
+    unsigned *step;
+    int *err;                            // sticky: a likelihood call gave up
+    const int *like_err;                 // the likelihood's flag of its last call (or NULL)
+    RecCtl *rec;
+};
+
+__device__ inline double ln_prior(const double *x, const Dev &s) {
+    for (int q = 0; q < D; q++)
+        if (!(x[q] >= s.lo[q] && x[q] <= s.hi[q])) return -INFINITY;
+    return 0.0;
+}
+
+// Gaussian test target, every operation rounded as written
+__device__ inline double gauss_lnl(const double *x, const Dev &s) {
+    double acc = 0.0;
+    for (int q = 0; q < D; q++) {
+        const double r = __ddiv_rn(__dsub_rn(x[q], s.mean[q]), s.sig[q]);
+        acc = __dadd_rn(acc, __dmul_rn(r, r));
+    }
+    return __dmul_rn(-0.5, acc);
+}
+
+// LISA frame -> SSB frame.  The constellation of the response model is a fixed triangle
+// rotated by Q = Rz(alpha) Ry(-pi/3) Rz(-alpha), alpha = 2 pi t / yr; the LISA frame is
+// the one in which the triangle is at rest, at the arrival time t_L (absolute seconds).
+__device__ inline void lisa_to_ssb(double tL, double lamL, double betL, double psiL, double *t,
+                                   double *lam, double *bet, double *psi) {
+    double sa, ca;
+    sincos(2.0 * kPi * tL / kYearS, &sa, &ca);
+    const double h = 0.8660254037844386467637231707529362;  // sqrt(3)/2
+    const double Q[3][3] = {{0.5 * ca * ca + sa * sa, -0.5 * ca * sa, -h * ca},
+                            {-0.5 * ca * sa, 0.5 * sa * sa + ca * ca, -h * sa},
+                            {h * ca, h * sa, 0.5}};
+    double sl, cl, sb, cb, sp, cp;
+    sincos(lamL, &sl, &cl);
+    sincos(betL, &sb, &cb);
+    sincos(psiL, &sp, &cp);
+    // direction to the source and polarisation axis cos(psi) u + sin(psi) v in the L frame
+    const double nL[3] = {cb * cl, cb * sl, sb};
+    const double pL[3] = {cp * sl - sp * sb * cl, -cp * cl - sp * sb * sl, sp * cb};
+    double n[3], p[3];
+    for (int i = 0; i < 3; i++) {
+        n[i] = Q[i][0] * nL[0] + Q[i][1] * nL[1] + Q[i][2] * nL[2];
+        p[i] = Q[i][0] * pL[0] + Q[i][1] * pL[1] + Q[i][2] * pL[2];
+    }
+    double l = atan2(n[1], n[0]);
+    if (l < 0.0) l += 2.0 * kPi;
+    const double nz = fmin(1.0, fmax(-1.0, n[2]));
+    // u = (n_y, -n_x, 0)/rho and v = (-n_z n_x, -n_z n_y, rho^2)/rho with rho = cos(beta)
+    const double rho2 = n[0] * n[0] + n[1] * n[1];
+    double ps = atan2(-nz * (p[0] * n[0] + p[1] * n[1]) + p[2] * rho2, p[0] * n[1] - p[1] * n[0]);
+    ps = fmod(ps, kPi);
+    if (ps < 0.0) ps += kPi;
+    // arrival at the centre t_L = t + k . p0(t) with k = -n: fixed point in t
+    double tt = tL;
+    for (int it = 0; it < 6; it++) {
+        double s2, c2;
+        sincos(2.0 * kPi * tt / kYearS, &s2, &c2);
+        tt = tL + kAuS * (n[0] * c2 + n[1] * s2);
+    }
+    *t = tt;
+    *lam = l;
+    *bet = asin(nz);
+    *psi = ps;
+}
+
+// sampling coordinates of Table I -> physical parameters of the likelihood
+__device__ inline void to_physical(const double *x, int lisa_frame, double t0, double *th) {
+    th[0] = exp(x[0]);
+    th[1] = x[1];
+    th[2] = x[2];
+    th[3] = x[3];
+    th[4] = exp(x[4]);
+    th[5] = x[5];
+    th[6] = acos(x[6]);
+    if (lisa_frame) {
+        double t, l, b, p;
+        lisa_to_ssb(exp(x[10]) + t0, x[7], asin(x[8]), x[9], &t, &l, &b, &p);
+        th[7] = l;
+        th[8] = b;
+        th[9] = p;
+        th[10] = t - t0;
+    } else {
+        th[7] = x[7];
+        th[8] = asin(x[8]);
+        th[9] = x[9];
+        th[10] = exp(x[10]);
+    }
+}
+
+// parameters the likelihood rejects (lnL = -inf, no dense work)
+__device__ inline void invalid_params(double *th) {
+    th[0] = __longlong_as_double(0x7ff8000000000000LL);
+    for (int q = 1; q < D; q++) th[q] = 0.0;
+}
+
+// ------------------------------------------------------------------ kernels
+// ln pi and the likelihood input (or the Gaussian ln L) of walkers c*T*H .. (c+1)*T*H-1
+__global__ void init_kernel(Dev s, int c) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.T * s.H) return;
+    const int i = c * s.T * s.H + p;
+    const double *x = s.x + (size_t)i * D;
+    const double lp = ln_prior(x, s);
+    s.lnp[i] = lp;
+    if (s.target == LISA_TARGET_GAUSSIAN) {
+        s.lnl[i] = gauss_lnl(x, s);
+    } else if (isfinite(lp)) {
+        to_physical(x, s.lisa_frame, s.t0, s.pth + (size_t)p * D);
+    } else {
+        invalid_params(s.pth + (size_t)p * D);
+    }
+}
+
+// stretch proposals (Eqs. (14)-(15)) for the walkers of half h of every temperature
+__global__ void propose_kernel(Dev s, int h) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.T * s.H) return;
+    const int t = p / s.H, kk = p - t * s.H, k = h * s.H + kk;
+    const U4 r = philox(*s.step, (uint32_t)h, (uint32_t)t, (uint32_t)k, s.k0, s.k1);
+    int jj = (int)__dmul_rn(unit(r.v[0]), (double)s.H);
+    if (jj > s.H - 1) jj = s.H - 1;
+    const int j = (1 - h) * s.H + jj;
+    // z = (1 + (a - 1) u)^2 / a: the inverse CDF of g(z) ~ 1/sqrt(z) on [1/a, a]
+    const double g = __dadd_rn(__dmul_rn(__dsub_rn(s.a, 1.0), unit(r.v[1])), 1.0);
+    const double z = __ddiv_rn(__dmul_rn(g, g), s.a);
+    const double *xk = s.x + ((size_t)t * s.W + k) * D;
+    const double *xj = s.x + ((size_t)t * s.W + j) * D;
+    double y[D];
+    for (int q = 0; q < D; q++) y[q] = __dadd_rn(xj[q], __dmul_rn(z, __dsub_rn(xk[q], xj[q])));
+    const double lp = ln_prior(y, s);
+    double *yo = s.y + (size_t)p * D;
+    for (int q = 0; q < D; q++) yo[q] = y[q];
+    s.z[p] = z;
+    s.py[p] = lp;
+    if (s.target == LISA_TARGET_GAUSSIAN)
+        s.ly[p] = gauss_lnl(y, s);
+    else if (isfinite(lp))
+        to_physical(y, s.lisa_frame, s.t0, s.pth + (size_t)p * D);
+    else
+        invalid_params(s.pth + (size_t)p * D);
+}
+
+// tempered Metropolis-Hastings acceptance of the stretch move (Eq. (16), Sec. III.B)
+__global__ void accept_kernel(Dev s, int h) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.T * s.H) return;
+    if (*s.err) return;
+    if (s.like_err && *s.like_err) {
+        atomicOr(s.err, 1);
+        return;
+    }
+    const int t = p / s.H, kk = p - t * s.H, k = h * s.H + kk;
+    const size_t i = (size_t)t * s.W + k;
+    const U4 r = philox(*s.step, (uint32_t)h, (uint32_t)t, (uint32_t)k, s.k0, s.k1);
+    const double py = s.py[p], ly = s.ly[p], beta = s.betas[t];
+    double lr = __dsub_rn(__dadd_rn(__dmul_rn((double)(D - 1), log(s.z[p])), py), s.lnp[i]);
+    if (beta > 0.0) lr = __dadd_rn(lr, __dmul_rn(beta, __dsub_rn(ly, s.lnl[i])));
+    if (isfinite(py) && log(unit(r.v[2])) < lr) {
+        const double *yo = s.y + (size_t)p * D;
+        double *xo = s.x + i * D;
+        for (int q = 0; q < D; q++) xo[q] = yo[q];
+        s.lnl[i] = ly;
+        s.lnp[i] = py;
+        atomicAdd(s.acc + 2 * t, 1ULL);
+    }
+}
+
+// temperature swaps (Eq. (17)) from the hottest pair down, the ladder update of Vousden,
+// Farr & Mandel (2016), the chain record and the step counter; one block
+__global__ void __launch_bounds__(kSwapThreads) swap_kernel(Dev s) {
+    __shared__ int cnt[kMaxT];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < kMaxT; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    const unsigned step = *s.step;
+    for (int w = tid; w < s.W; w += blockDim.x) {
+        for (int t = s.T - 2; t >= 0; t--) {
+            const U4 r = philox(step, 2u, (uint32_t)t, (uint32_t)w, s.k0, s.k1);
+            const size_t i = (size_t)t * s.W + w, j = (size_t)(t + 1) * s.W + w;
+            const double la =
+                __dmul_rn(__dsub_rn(s.betas[t], s.betas[t + 1]), __dsub_rn(s.lnl[j], s.lnl[i]));
+            if (log(unit(r.v[0])) < la) {
+                double *xi = s.x + i * D, *xj = s.x + j * D;
+                for (int q = 0; q < D; q++) {
+                    const double v = xi[q];
+                    xi[q] = xj[q];
+                    xj[q] = v;
+                }
+                double v = s.lnl[i];
+                s.lnl[i] = s.lnl[j];
+                s.lnl[j] = v;
+                v = s.lnp[i];
+                s.lnp[i] = s.lnp[j];
+                s.lnp[j] = v;
+                atomicAdd(&cnt[t], 1);
+            }
+        }
+    }
+    __syncthreads();
+    RecCtl *rc = s.rec;
+    const int row = rc->i;
+    if (rc->chain || rc->lnl) {
+        for (int w = tid; w < s.W; w += blockDim.x) {
+            if (rc->chain)
+                for (int q = 0; q < D; q++)
+                    rc->chain[((size_t)row * s.W + w) * D + q] = s.x[(size_t)w * D + q];
+            if (rc->lnl) rc->lnl[(size_t)row * s.W + w] = s.lnl[w];
+        }
+    }
+    if (tid == 0) {
+        double A[kMaxT];
+        for (int t = 0; t < s.T; t++) {
+            s.acc[2 * t + 1] += (unsigned long long)s.W;
+            A[t] = 0.0;
+        }
+        for (int t = 0; t + 1 < s.T; t++) {
+            s.swaps[2 * t] += (unsigned long long)cnt[t];
+            s.swaps[2 * t + 1] += (unsigned long long)s.W;
+            A[t] = __ddiv_rn((double)cnt[t], (double)s.W);
+        }
+        if (s.adaptive && s.T >= 3) {
+            // S_g = ln(T_{g+1} - T_g) moves by kappa (A_g - A_{g+1}); T_0 and T_{T-1} fixed
+            const double kappa = __ddiv_rn(s.lag, __dmul_rn(s.nu, __dadd_rn((double)step, s.lag)));
+            double gap[kMaxT];
+            for (int g = 0; g + 1 < s.T - 1; g++) {
+                const double dS = __dmul_rn(kappa, __dsub_rn(A[g], A[g + 1]));
+                gap[g] = __dmul_rn(__dsub_rn(__ddiv_rn(1.0, s.betas[g + 1]), __ddiv_rn(1.0, s.betas[g])),
+                                   exp(dS));
+            }
+            double Tacc = __ddiv_rn(1.0, s.betas[0]);
+            for (int g = 0; g + 1 < s.T - 1; g++) {
+                Tacc = __dadd_rn(Tacc, gap[g]);
+                s.betas[g + 1] = __ddiv_rn(1.0, Tacc);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        rc->i = row + 1;
+        *s.step = step + 1;
+    }
+}
+
+__global__ void to_physical_kernel(const double *x, int n, int lisa_frame, double t0, double *th) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xi[D], o[D];
+    for (int q = 0; q < D; q++) xi[q] = x[(size_t)i * D + q];
+    to_physical(xi, lisa_frame, t0, o);
+    for (int q = 0; q < D; q++) th[(size_t)i * D + q] = o[q];
+}
+
+// per-walker mean and lag-0 autocovariance (Eqs. (20)-(21))
+__global__ void acf_stats_kernel(const double *c, int n, int W, int stride, int off, double *mu,
+                                 double *c0) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    double m = 0.0;
+    for (int i = 0; i < n; i++) m += c[((size_t)i * W + w) * stride + off];
+    m /= n;
+    double v = 0.0;
+    for (int i = 0; i < n; i++) {
+        const double e = c[((size_t)i * W + w) * stride + off] - m;
+        v += e * e;
+    }
+    mu[w] = m;
+    c0[w] = v / n;
+}
+
+// rho_w(lag) = c_w(lag) / c_w(0) for lags lag0 .. lag0 + gridDim.y - 1 (Eq. (19))
+__global__ void acf_lag_kernel(const double *c, int n, int W, int stride, int off, int lag0,
+                               const double *mu, const double *c0, double *rho) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lag = lag0 + blockIdx.y;
+    if (w >= W || lag >= n) return;
+    const double m = mu[w];
+    double acc = 0.0;
+    for (int i = 0; i + lag < n; i++)
+        acc += (c[((size_t)i * W + w) * stride + off] - m) *
+               (c[((size_t)(i + lag) * W + w) * stride + off] - m);
+    rho[(size_t)blockIdx.y * W + w] = c0[w] > 0.0 ? acc / (double)(n - lag) / c0[w] : 0.0;
+}
+
+int blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host handle
+struct lisa_sampler {
+    lisa_sampler_config cfg;
+    lisa_like_t *like = nullptr;
+    lisa::LikeInfo li{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    Dev dev{};
+    RecCtl *h_rec = nullptr;  // pinned staging
+    int *h_err = nullptr;
+    double timeout_s = 60.0;
+    bool have_state = false;
+    int launches = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int g_launches = 0;
+    cudaEvent_t done = nullptr;
+    std::vector<void *> bufs;
+    std::string err;
+};
+
+namespace {
+
+lisa_status sfail(lisa_sampler_t *s, lisa_status st, const std::string &m) {
+    if (s) s->err = m;
+    return st;
+}
+
+lisa_status scuda(lisa_sampler_t *s, cudaError_t e, const char *what) {
+    return sfail(s, e == cudaErrorMemoryAllocation ? LISA_ERR_OOM : LISA_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SCK(call, what)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return scuda(s, e_, what);    \
+    } while (0)
+
+template <typename T>
+cudaError_t salloc(lisa_sampler_t *s, T **p, size_t n) {
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess) s->bufs.push_back(*p);
+    return e;
+}
+
+lisa_status wait_done(lisa_sampler_t *s, double limit_s) {
+    SCK(cudaEventRecord(s->done, s->stream), "cudaEventRecord");
+    const auto t0 = std::chrono::steady_clock::now();
+    int polls = 0;
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(s->done);
+        if (e == cudaSuccess) return LISA_OK;
+        if (e != cudaErrorNotReady) return scuda(s, e, "device work failed");
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit_s) return sfail(s, LISA_ERR_TIMEOUT, "sampler did not finish within the timeout");
+        if (++polls > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// the kernels of one step on the sampler's stream
+lisa_status enqueue_step(lisa_sampler_t *s, int *nl) {
+    const int n = s->dev.T * s->dev.H;
+    int count = 0;
+    for (int h = 0; h < 2; h++) {
+        propose_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(s->dev, h);
+        SCK(cudaGetLastError(), "proposal kernel launch");
+        count++;
+        if (s->dev.target == LISA_TARGET_LIKELIHOOD) {
+            int l = 0;
+            lisa_status st = lisa::like_enqueue(s->like, s->dev.pth, n, s->dev.ly, s->stream, &l);
+            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->like));
+            count += l;
+        }
+        accept_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(s->dev, h);
+        SCK(cudaGetLastError(), "acceptance kernel launch");
+        count++;
+    }
+    swap_kernel<<<1, kSwapThreads, 0, s->stream>>>(s->dev);
+    SCK(cudaGetLastError(), "swap kernel launch");
+    count++;
+    *nl = count;
+    return LISA_OK;
+}
+
+void drop_graph(lisa_sampler_t *s) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+}
+
+lisa_status capture(lisa_sampler_t *s) {
+    drop_graph(s);
+    cudaGraph_t g = nullptr;
+    SCK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    int nl = 0;
+    lisa_status st = enqueue_step(s, &nl);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (st != LISA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return scuda(s, e, "graph capture");
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->gexec = nullptr;
+        return scuda(s, e, "graph instantiation");
+    }
+    s->g_launches = nl;
+    return LISA_OK;
+}
+
+bool valid_box(const double *lo, const double *hi) {
+    for (int q = 0; q < D; q++)
+        if (!(std::isfinite(lo[q]) && std::isfinite(hi[q]) && lo[q] < hi[q])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lisa_sampler_default_config(lisa_sampler_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->n_temps = 8;
+    c->n_walkers = 256;
+    c->a = 1.15;
+    c->ladder_ratio = 2.04807;
+    c->t_max_inf = 1;
+    c->adaptive = 1;
+    c->adapt_lag = 10000.0;
+    c->adapt_time = 100.0;
+    c->seed = 1;
+    // Table I
+    const double lo[D] = {std::log(1e3), 0.05, -0.99, -0.99, std::log(0.044), 0.0, -1.0, 0.0,
+                          -1.0, 0.0, 0.0};
+    const double hi[D] = {std::log(1e9), 1.0, 0.99, 0.99, std::log(1298.0), 2.0 * kPi, 1.0,
+                          2.0 * kPi, 1.0, kPi, std::log(3.15576e8)};
+    std::memcpy(c->lower, lo, sizeof(lo));
+    std::memcpy(c->upper, hi, sizeof(hi));
+    c->lisa_frame = 1;
+    c->target = LISA_TARGET_LIKELIHOOD;
+    for (int q = 0; q < D; q++) c->gauss_sigma[q] = 1.0;
+    c->use_graphs = 1;
+}
+
+lisa_status lisa_sampler_create(lisa_like_t *like, const lisa_sampler_config *cfg,
+                                lisa_sampler_t **out) {
+    lisa::set_thread_error("");
+    auto bad = [](const char *m) {
+        lisa::set_thread_error(m);
+        return LISA_ERR_ARG;
+    };
+    if (!cfg || !out) return bad("NULL config or output pointer");
+    *out = nullptr;
+    const int T = cfg->n_temps, W = cfg->n_walkers;
+    if (T < 1 || T > kMaxT) return bad("n_temps must be in [1, 64]");
+    if (W < 4 || (W & 1) || W > (1 << 16)) return bad("n_walkers must be even and in [4, 65536]");
+    if (!(cfg->a > 1.0) || !std::isfinite(cfg->a)) return bad("stretch scale a must be > 1");
+    if (!(cfg->ladder_ratio > 1.0) || !std::isfinite(cfg->ladder_ratio))
+        return bad("ladder_ratio must be > 1");
+    if (cfg->adaptive && !(cfg->adapt_lag > 0.0 && cfg->adapt_time > 0.0))
+        return bad("adapt_lag and adapt_time must be > 0");
+    if (!valid_box(cfg->lower, cfg->upper)) return bad("prior bounds must be finite with lower < upper");
+    if (cfg->target != LISA_TARGET_LIKELIHOOD && cfg->target != LISA_TARGET_GAUSSIAN)
+        return bad("unknown target");
+    if (cfg->target == LISA_TARGET_GAUSSIAN)
+        for (int q = 0; q < D; q++)
+            if (!(cfg->gauss_sigma[q] > 0.0) || !std::isfinite(cfg->gauss_mean[q]))
+                return bad("Gaussian target needs finite means and sigma > 0");
+    lisa::LikeInfo li{};
+    if (cfg->target == LISA_TARGET_LIKELIHOOD) {
+        if (!like) return bad("the likelihood target needs a lisa_like handle");
+        li = lisa::like_info(like);
+        if (!li.have_data) {
+            lisa::set_thread_error("lisa_like_set_data must be called before creating the sampler");
+            return LISA_ERR_STATE;
+        }
+        if ((int64_t)T * (W / 2) > li.max_batch)
+            return bad("the likelihood's max_batch must be >= n_temps * n_walkers / 2");
+    }
+    lisa_sampler_t *s = new lisa_sampler();
+    s->cfg = *cfg;
+    s->like = cfg->target == LISA_TARGET_LIKELIHOOD ? like : nullptr;
+    s->li = li;
+    lisa_status st = LISA_OK;
+    do {
+        int dev = 0;
+        cudaError_t e = cudaSuccess;
+        if (s->like) {
+            dev = li.device;
+            s->stream = li.stream;
+            s->timeout_s = cfg->timeout_s > 0.0 ? cfg->timeout_s : li.timeout_s;
+            e = cudaSetDevice(dev);
+        } else {
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+            s->own_stream = e == cudaSuccess;
+            s->timeout_s = cfg->timeout_s > 0.0 ? cfg->timeout_s : 60.0;
+        }
+        if (e != cudaSuccess) {
+            st = scuda(s, e, "device setup");
+            break;
+        }
+        s->device = dev;
+        Dev &d = s->dev;
+        d.T = T;
+        d.W = W;
+        d.H = W / 2;
+        d.target = cfg->target;
+        d.lisa_frame = cfg->lisa_frame ? 1 : 0;
+        d.adaptive = cfg->adaptive ? 1 : 0;
+        d.k0 = (uint32_t)cfg->seed;
+        d.k1 = (uint32_t)(cfg->seed >> 32);
+        d.a = cfg->a;
+        d.t0 = li.t0;
+        d.lag = cfg->adapt_lag;
+        d.nu = cfg->adapt_time;
+        for (int q = 0; q < D; q++) {
+            d.lo[q] = cfg->lower[q];
+            d.hi[q] = cfg->upper[q];
+            d.mean[q] = cfg->gauss_mean[q];
+            d.sig[q] = cfg->gauss_sigma[q];
+        }
+        const size_t TW = (size_t)T * W, TH = (size_t)T * d.H;
+        if ((e = salloc(s, &d.x, TW * D)) != cudaSuccess || (e = salloc(s, &d.lnl, TW)) != cudaSuccess ||
+            (e = salloc(s, &d.lnp, TW)) != cudaSuccess || (e = salloc(s, &d.betas, (size_t)T)) != cudaSuccess ||
+            (e = salloc(s, &d.y, TH * D)) != cudaSuccess || (e = salloc(s, &d.pth, TH * D)) != cudaSuccess ||
+            (e = salloc(s, &d.ly, TH)) != cudaSuccess || (e = salloc(s, &d.z, TH)) != cudaSuccess ||
+            (e = salloc(s, &d.py, TH)) != cudaSuccess || (e = salloc(s, &d.acc, 2 * (size_t)T)) != cudaSuccess ||
+            (e = salloc(s, &d.swaps, 2 * (size_t)T)) != cudaSuccess || (e = salloc(s, &d.step, 1)) != cudaSuccess ||
+            (e = salloc(s, &d.err, 1)) != cudaSuccess || (e = salloc(s, &d.rec, 1)) != cudaSuccess) {
+            st = scuda(s, e, "device allocation (sampler state)");
+            break;
+        }
+        d.like_err = s->like ? li.err_flag : nullptr;
+        if ((e = cudaMallocHost(&s->h_rec, sizeof(RecCtl))) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_err, sizeof(int))) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess) {
+            st = scuda(s, e, "host staging");
+            break;
+        }
+        std::memset(s->h_rec, 0, sizeof(RecCtl));
+        if ((e = cudaMemsetAsync(d.rec, 0, sizeof(RecCtl), s->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.err, 0, sizeof(int), s->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.step, 0, sizeof(unsigned), s->stream)) != cudaSuccess) {
+            st = scuda(s, e, "cudaMemsetAsync");
+            break;
+        }
+        std::vector<double> b(T);
+        for (int t = 0; t < T; t++) b[t] = 1.0 / std::pow(cfg->ladder_ratio, (double)t);
+        if (cfg->t_max_inf && T > 1) b[T - 1] = 0.0;
+        st = lisa_sampler_set_ladder(s, b.data());
+    } while (0);
+    if (st != LISA_OK) {
+        lisa::set_thread_error(s->err);
+        lisa_sampler_destroy(s);
+        return st;
+    }
+    *out = s;
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_set_ladder(lisa_sampler_t *s, const double *betas) {
+    if (!s) return LISA_ERR_ARG;
+    if (!betas) return sfail(s, LISA_ERR_ARG, "NULL ladder");
+    const int T = s->dev.T;
+    for (int t = 0; t < T; t++) {
+        if (!(betas[t] >= 0.0 && betas[t] <= 1.0)) return sfail(s, LISA_ERR_ARG, "betas must be in [0, 1]");
+        if (t > 0 && !(betas[t] <= betas[t - 1]))
+            return sfail(s, LISA_ERR_ARG, "betas must not increase with the temperature index");
+    }
+    if (T > 1 && s->dev.adaptive && T >= 3 && !(betas[T - 2] > 0.0))
+        return sfail(s, LISA_ERR_ARG, "only the hottest beta may be 0");
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    SCK(cudaMemcpyAsync(s->dev.betas, betas, sizeof(double) * T, cudaMemcpyHostToDevice, s->stream),
+        "ladder upload");
+    return wait_done(s, s->timeout_s);
+}
+
+lisa_status lisa_sampler_set_state(lisa_sampler_t *s, const double *x, uint32_t step) {
+    if (!s) return LISA_ERR_ARG;
+    if (!x) return sfail(s, LISA_ERR_ARG, "NULL state");
+    Dev &d = s->dev;
+    const size_t TW = (size_t)d.T * d.W;
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    SCK(cudaMemcpyAsync(d.x, x, sizeof(double) * TW * D, cudaMemcpyHostToDevice, s->stream),
+        "state upload");
+    *s->h_err = (int)step;
+    SCK(cudaMemcpyAsync(d.step, s->h_err, sizeof(unsigned), cudaMemcpyHostToDevice, s->stream),
+        "step upload");
+    SCK(cudaMemsetAsync(d.acc, 0, sizeof(unsigned long long) * 2 * d.T, s->stream), "cudaMemsetAsync");
+    SCK(cudaMemsetAsync(d.swaps, 0, sizeof(unsigned long long) * 2 * d.T, s->stream), "cudaMemsetAsync");
+    SCK(cudaMemsetAsync(d.err, 0, sizeof(int), s->stream), "cudaMemsetAsync");
+    const int n = d.T * d.H;
+    for (int c = 0; c < 2; c++) {
+        init_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(d, c);
+        SCK(cudaGetLastError(), "init kernel launch");
+        if (d.target == LISA_TARGET_LIKELIHOOD) {
+            lisa_status st = lisa::like_enqueue(s->like, d.pth, n, d.lnl + (size_t)c * n, s->stream, nullptr);
+            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->like));
+            // the likelihood's own flag of this call
+            SCK(cudaMemcpyAsync(s->h_err, s->li.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
+                "flag download");
+            lisa_status w = wait_done(s, s->timeout_s);
+            if (w != LISA_OK) return w;
+            if (*s->h_err)
+                return sfail(s, LISA_ERR_TIMEOUT, "a likelihood wait gave up while evaluating the state");
+        }
+    }
+    lisa_status w = wait_done(s, s->timeout_s);
+    if (w != LISA_OK) return w;
+    s->have_state = true;
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_run(lisa_sampler_t *s, int n_steps, double *d_chain, double *d_lnl) {
+    if (!s) return LISA_ERR_ARG;
+    if (!s->have_state) return sfail(s, LISA_ERR_STATE, "set_state must be called first");
+    if (n_steps < 1) return sfail(s, LISA_ERR_ARG, "n_steps must be >= 1");
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    s->h_rec->chain = d_chain;
+    s->h_rec->lnl = d_lnl;
+    s->h_rec->i = 0;
+    SCK(cudaMemcpyAsync(s->dev.rec, s->h_rec, sizeof(RecCtl), cudaMemcpyHostToDevice, s->stream),
+        "record upload");
+    if (s->cfg.use_graphs) {
+        // likelihood buffers can change with set_data or a new tile shape: capture afresh
+        lisa_status st = capture(s);
+        if (st != LISA_OK) return st;
+        for (int i = 0; i < n_steps; i++) SCK(cudaGraphLaunch(s->gexec, s->stream), "cudaGraphLaunch");
+        s->launches = s->g_launches;
+    } else {
+        for (int i = 0; i < n_steps; i++) {
+            int nl = 0;
+            lisa_status st = enqueue_step(s, &nl);
+            if (st != LISA_OK) return st;
+            s->launches = nl;
+        }
+    }
+    SCK(cudaMemcpyAsync(s->h_err, s->dev.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
+        "flag download");
+    lisa_status w = wait_done(s, s->timeout_s * n_steps);
+    if (w != LISA_OK) return w;
+    if (*s->h_err)
+        return sfail(s, LISA_ERR_TIMEOUT,
+                     "a likelihood wait gave up during the run; the state stopped changing there");
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_get_state(lisa_sampler_t *s, double *x, double *lnl, double *betas,
+                                   uint32_t *step) {
+    if (!s) return LISA_ERR_ARG;
+    const Dev &d = s->dev;
+    const size_t TW = (size_t)d.T * d.W;
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (x) SCK(cudaMemcpyAsync(x, d.x, sizeof(double) * TW * D, cudaMemcpyDeviceToHost, s->stream), "download");
+    if (lnl) SCK(cudaMemcpyAsync(lnl, d.lnl, sizeof(double) * TW, cudaMemcpyDeviceToHost, s->stream), "download");
+    if (betas) SCK(cudaMemcpyAsync(betas, d.betas, sizeof(double) * d.T, cudaMemcpyDeviceToHost, s->stream), "download");
+    SCK(cudaMemcpyAsync(s->h_err, d.step, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream), "download");
+    lisa_status w = wait_done(s, s->timeout_s);
+    if (w != LISA_OK) return w;
+    if (step) *step = (uint32_t)*s->h_err;
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_get_counts(lisa_sampler_t *s, int64_t *acc, int64_t *swaps) {
+    if (!s) return LISA_ERR_ARG;
+    const Dev &d = s->dev;
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (acc) SCK(cudaMemcpyAsync(acc, d.acc, sizeof(int64_t) * 2 * d.T, cudaMemcpyDeviceToHost, s->stream), "download");
+    if (swaps) SCK(cudaMemcpyAsync(swaps, d.swaps, sizeof(int64_t) * 2 * d.T, cudaMemcpyDeviceToHost, s->stream), "download");
+    return wait_done(s, s->timeout_s);
+}
+
+int lisa_sampler_step_launches(const lisa_sampler_t *s) { return s ? s->launches : 0; }
+
+void lisa_sampler_destroy(lisa_sampler_t *s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graph(s);
+    for (void *p : s->bufs) cudaFree(p);
+    if (s->h_rec) cudaFreeHost(s->h_rec);
+    if (s->h_err) cudaFreeHost(s->h_err);
+    if (s->done) cudaEventDestroy(s->done);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char *lisa_sampler_last_error(const lisa_sampler_t *s) {
+    return s ? s->err.c_str() : lisa::thread_error();
+}
+
+lisa_status lisa_sampler_to_physical(const double *d_x, int n, int lisa_frame, double t0,
+                                     double *d_th, void *stream) {
+    lisa::set_thread_error("");
+    if (!d_x || !d_th || n < 0 || !std::isfinite(t0)) {
+        lisa::set_thread_error("NULL pointer, negative n or non-finite t0");
+        return LISA_ERR_ARG;
+    }
+    if (n == 0) return LISA_OK;
+    to_physical_kernel<<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>(d_x, n, lisa_frame, t0, d_th);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        lisa::set_thread_error(std::string("conversion kernel launch: ") + cudaGetErrorString(e));
+        return LISA_ERR_CUDA;
+    }
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_sky_mode_init(const double *xc, const double *scale, const double *lower,
+                                       const double *upper, int T, int W, uint64_t seed,
+                                       double *x_out) {
+    lisa::set_thread_error("");
+    if (!xc || !scale || !lower || !upper || !x_out || T < 1 || W < 8 || W % 8) {
+        lisa::set_thread_error("NULL pointer, T < 1, or W not a positive multiple of 8");
+        return LISA_ERR_ARG;
+    }
+    if (!valid_box(lower, upper)) {
+        lisa::set_thread_error("prior bounds must be finite with lower < upper");
+        return LISA_ERR_ARG;
+    }
+    // a key of its own, so that the jitter is independent of the sampler's draws
+    const uint32_t k0 = (uint32_t)seed ^ 0x5BD1E995u, k1 = (uint32_t)(seed >> 32) ^ 0x1B873593u;
+    for (int t = 0; t < T; t++)
+        for (int w = 0; w < W; w++) {
+            double g[12];
+            for (int blk = 0; blk < 3; blk++) {
+                // Box-Muller on two Philox pairs
+                const U4 r = philox((uint32_t)t, (uint32_t)w, 0x51u, (uint32_t)blk, k0, k1);
+                for (int pr = 0; pr < 2; pr++) {
+                    const double u1 = unit(r.v[2 * pr]), u2 = unit(r.v[2 * pr + 1]);
+                    const double rad = std::sqrt(-2.0 * std::log(u1));
+                    g[4 * blk + 2 * pr] = rad * std::cos(2.0 * kPi * u2);
+                    g[4 * blk + 2 * pr + 1] = rad * std::sin(2.0 * kPi * u2);
+                }
+            }
+            double *x = x_out + ((size_t)t * W + w) * D;
+            const int mode = w % 8;
+            for (int q = 0; q < D; q++) {
+                double v = xc[q] + scale[q] * g[q];
+                if (q == 7) v += (mode % 4) * 0.5 * kPi;
+                if (q == 8 && mode >= 4) v = -xc[q] + scale[q] * g[q];
+                const double lo = lower[q], hi = upper[q];
+                if (q == 7) {  // longitude: periodic
+                    const double span = hi - lo;
+                    v = lo + std::fmod(v - lo, span);
+                    if (v < lo) v += span;
+                    if (v >= hi) v = lo;
+                } else {
+                    for (int it = 0; it < 64 && (v < lo || v > hi); it++) v = v < lo ? 2.0 * lo - v : 2.0 * hi - v;
+                    v = std::fmin(hi, std::fmax(lo, v));
+                }
+                x[q] = v;
+            }
+        }
+    return LISA_OK;
+}
+
+lisa_status lisa_autocorr_time(const double *d_chain, int n, int W, int stride, int offset,
+                               double *tau, double *rho, void *stream) {
+    lisa::set_thread_error("");
+    if (!d_chain || !tau || n < 2 || W < 1 || stride < 1 || offset < 0 || offset >= stride) {
+        lisa::set_thread_error("need a chain, n >= 2, W >= 1 and 0 <= offset < stride");
+        return LISA_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int kLags = 256;
+    double *mu = nullptr, *c0 = nullptr, *rb = nullptr;
+    std::vector<double> h_c0(W), h_rho((size_t)kLags * W);
+    std::string msg;
+    cudaError_t e = cudaMalloc(&mu, sizeof(double) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c0, sizeof(double) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&rb, sizeof(double) * kLags * W);
+    if (e == cudaSuccess) {
+        acf_stats_kernel<<<blocks_for(W), kThreads, 0, st>>>(d_chain, n, W, stride, offset, mu, c0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_c0.data(), c0, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int used = 0;
+    for (int w = 0; w < W && e == cudaSuccess; w++) used += h_c0[w] > 0.0;
+    double t_est = NAN;
+    if (rho) std::memset(rho, 0, sizeof(double) * n);
+    if (e == cudaSuccess && used > 0) {
+        if (rho) rho[0] = 1.0;
+        t_est = 1.0;
+        bool done = false;
+        for (int lag0 = 1; lag0 < n && !done && e == cudaSuccess; lag0 += kLags) {
+            const int nl = std::min(kLags, n - lag0);
+            acf_lag_kernel<<<dim3(blocks_for(W), nl), kThreads, 0, st>>>(d_chain, n, W, stride, offset,
+                                                                         lag0, mu, c0, rb);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_rho.data(), rb, sizeof(double) * nl * W, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            for (int l = 0; l < nl && e == cudaSuccess; l++) {
+                double r = 0.0;
+                for (int w = 0; w < W; w++) r += h_rho[(size_t)l * W + w];
+                r /= used;
+                const int M = lag0 + l;
+                if (rho) rho[M] = r;
+                t_est += 2.0 * r;
+                if ((double)M >= 5.0 * t_est) {
+                    done = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (mu) cudaFree(mu);
+    if (c0) cudaFree(c0);
+    if (rb) cudaFree(rb);
+    if (e != cudaSuccess) {
+        lisa::set_thread_error(std::string("autocorrelation: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LISA_ERR_OOM : LISA_ERR_CUDA;
+    }
+    *tau = t_est;
+    return LISA_OK;
+}
+
+}  // extern "C"

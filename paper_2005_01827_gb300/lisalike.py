@@ -31,7 +31,15 @@ SYMBOLS = (
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
     "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
     "lisa_like_mode_inner",
+    # include/lisa_sampler.h
+    "lisa_sampler_default_config", "lisa_sampler_create", "lisa_sampler_set_ladder",
+    "lisa_sampler_set_state", "lisa_sampler_run", "lisa_sampler_get_state",
+    "lisa_sampler_get_counts", "lisa_sampler_step_launches", "lisa_sampler_destroy",
+    "lisa_sampler_last_error", "lisa_sampler_to_physical", "lisa_sampler_sky_mode_init",
+    "lisa_autocorr_time",
 )
+LISA_TARGET_LIKELIHOOD, LISA_TARGET_GAUSSIAN = 0, 1
+SAMPLER_NDIM = 11
 NOALLOC_SCRATCH_BYTES = 4194304
 NOALLOC_MAX_WALKER_MODE_KNOTS = 8192
 NOALLOC_MAX_ITEMS = 16384
@@ -47,6 +55,28 @@ class lisa_like_config(C.Structure):
         ("device", C.c_int),
         ("stream", C.c_void_p),
         ("max_batch", C.c_int),
+        ("timeout_s", C.c_double),
+    ]
+
+
+class lisa_sampler_config(C.Structure):
+    _fields_ = [
+        ("n_temps", C.c_int),
+        ("n_walkers", C.c_int),
+        ("a", C.c_double),
+        ("ladder_ratio", C.c_double),
+        ("t_max_inf", C.c_int),
+        ("adaptive", C.c_int),
+        ("adapt_lag", C.c_double),
+        ("adapt_time", C.c_double),
+        ("seed", C.c_uint64),
+        ("lower", C.c_double * 11),
+        ("upper", C.c_double * 11),
+        ("lisa_frame", C.c_int),
+        ("target", C.c_int),
+        ("gauss_mean", C.c_double * 11),
+        ("gauss_sigma", C.c_double * 11),
+        ("use_graphs", C.c_int),
         ("timeout_s", C.c_double),
     ]
 
@@ -116,6 +146,29 @@ def load(path: str = LIB_PATH):
     L.lisa_like_destroy.restype = None
     L.lisa_like_last_error.argtypes = [vp]
     L.lisa_like_last_error.restype = C.c_char_p
+    scfgp = C.POINTER(lisa_sampler_config)
+    u32, u64 = C.c_uint32, C.c_uint64
+    L.lisa_sampler_default_config.argtypes = [scfgp]
+    L.lisa_sampler_default_config.restype = None
+    L.lisa_sampler_create.argtypes = [vp, scfgp, C.POINTER(vp)]
+    L.lisa_sampler_set_ladder.argtypes = [vp, vp]
+    L.lisa_sampler_set_state.argtypes = [vp, vp, u32]
+    L.lisa_sampler_run.argtypes = [vp, i, vp, vp]
+    L.lisa_sampler_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(u32)]
+    L.lisa_sampler_get_counts.argtypes = [vp, vp, vp]
+    L.lisa_sampler_step_launches.argtypes = [vp]
+    L.lisa_sampler_destroy.argtypes = [vp]
+    L.lisa_sampler_destroy.restype = None
+    L.lisa_sampler_last_error.argtypes = [vp]
+    L.lisa_sampler_last_error.restype = C.c_char_p
+    L.lisa_sampler_to_physical.argtypes = [vp, i, i, d, vp, vp]
+    L.lisa_sampler_sky_mode_init.argtypes = [vp, vp, vp, vp, i, i, u64, vp]
+    L.lisa_autocorr_time.argtypes = [vp, i, i, i, i, dp, vp, vp]
+    for fn in ("lisa_sampler_create", "lisa_sampler_set_ladder", "lisa_sampler_set_state",
+               "lisa_sampler_run", "lisa_sampler_get_state", "lisa_sampler_get_counts",
+               "lisa_sampler_step_launches", "lisa_sampler_to_physical",
+               "lisa_sampler_sky_mode_init", "lisa_autocorr_time"):
+        getattr(L, fn).restype = i
     _lib = L
     return L
 
@@ -347,3 +400,176 @@ def psd_aet(f0, df, n_bins):
     out = np.empty((3, n_bins))
     lisa_psd_aet(f0, df, n_bins, out)
     return out
+
+
+# ------------------------------------------------------------------- sampler (lisa_sampler.h)
+
+def _scheck(st, s=None):
+    if st != LISA_OK:
+        raise LisaError(st, lisa_sampler_last_error(s))
+
+
+def lisa_sampler_default_config() -> lisa_sampler_config:
+    cfg = lisa_sampler_config()
+    load().lisa_sampler_default_config(C.byref(cfg))
+    return cfg
+
+
+def lisa_sampler_create(like_h, cfg: lisa_sampler_config):
+    s = C.c_void_p()
+    _scheck(load().lisa_sampler_create(like_h, C.byref(cfg), C.byref(s)))
+    return s
+
+
+def lisa_sampler_set_ladder(s, betas):
+    b = _f64(betas)
+    _scheck(load().lisa_sampler_set_ladder(s, _ptr(b)), s)
+
+
+def lisa_sampler_set_state(s, x, step=0):
+    xx = _f64(x)
+    _scheck(load().lisa_sampler_set_state(s, _ptr(xx), int(step)), s)
+
+
+def lisa_sampler_run(s, n_steps, d_chain=None, d_lnl=None):
+    _scheck(load().lisa_sampler_run(s, int(n_steps), _ptr(d_chain), _ptr(d_lnl)), s)
+
+
+def lisa_sampler_get_state(s, x=None, lnl=None, betas=None):
+    step = C.c_uint32()
+    _scheck(load().lisa_sampler_get_state(s, _ptr(x), _ptr(lnl), _ptr(betas), C.byref(step)), s)
+    return step.value
+
+
+def lisa_sampler_get_counts(s, acc=None, swaps=None):
+    _scheck(load().lisa_sampler_get_counts(s, _ptr(acc), _ptr(swaps)), s)
+
+
+def lisa_sampler_step_launches(s) -> int:
+    return load().lisa_sampler_step_launches(s)
+
+
+def lisa_sampler_destroy(s):
+    load().lisa_sampler_destroy(s)
+
+
+def lisa_sampler_last_error(s=None) -> str:
+    msg = load().lisa_sampler_last_error(s)
+    return msg.decode() if msg else ""
+
+
+def lisa_sampler_to_physical(d_x, n, lisa_frame, t0, d_th, stream=None):
+    st = None if stream is None else C.c_void_p(int(stream))
+    _scheck(load().lisa_sampler_to_physical(_ptr(d_x), int(n), int(bool(lisa_frame)), float(t0),
+                                            _ptr(d_th), st))
+
+
+def lisa_sampler_sky_mode_init(x_center, scale, lower, upper, T, W, seed, x_out):
+    xc, sc, lo, hi = _f64(x_center), _f64(scale), _f64(lower), _f64(upper)
+    _scheck(load().lisa_sampler_sky_mode_init(_ptr(xc), _ptr(sc), _ptr(lo), _ptr(hi), int(T),
+                                              int(W), int(seed), _ptr(x_out)))
+
+
+def lisa_autocorr_time(d_chain, n, W, stride=1, offset=0, rho=None, stream=None):
+    tau = C.c_double()
+    st = None if stream is None else C.c_void_p(int(stream))
+    _scheck(load().lisa_autocorr_time(_ptr(d_chain), int(n), int(W), int(stride), int(offset),
+                                      C.byref(tau), _ptr(rho), st))
+    return tau.value
+
+
+def sampler_config(**kw) -> lisa_sampler_config:
+    """lisa_sampler_default_config() with fields overridden by keyword."""
+    cfg = lisa_sampler_default_config()
+    for k, v in kw.items():
+        if k in ("lower", "upper", "gauss_mean", "gauss_sigma"):
+            arr = getattr(cfg, k)
+            for q, val in enumerate(np.asarray(v, dtype=np.float64).reshape(SAMPLER_NDIM)):
+                arr[q] = float(val)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class LisaSampler:
+    """Owns one sampler handle.  `like` is a LisaLike (or None for the Gaussian target).
+    Chains come back as numpy arrays; the device buffers are torch tensors."""
+
+    def __init__(self, like=None, **cfg):
+        self.cfg = sampler_config(**cfg)
+        self.T, self.W = self.cfg.n_temps, self.cfg.n_walkers
+        self.like = like
+        self.h = lisa_sampler_create(None if like is None else like.h, self.cfg)
+
+    def close(self):
+        if self.h is not None:
+            lisa_sampler_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_ladder(self, betas):
+        lisa_sampler_set_ladder(self.h, betas)
+
+    def set_state(self, x, step=0):
+        x = _f64(x).reshape(self.T, self.W, SAMPLER_NDIM)
+        lisa_sampler_set_state(self.h, x, step)
+
+    def run(self, n_steps, record=True):
+        """Run n_steps; returns (chain [n, W, 11], lnl [n, W]) of the coldest temperature
+        (None, None without record)."""
+        import torch
+
+        ch = lnl = None
+        if record:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            ch = torch.empty((n_steps, self.W, SAMPLER_NDIM), dtype=torch.float64, device=dev)
+            lnl = torch.empty((n_steps, self.W), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+        lisa_sampler_run(self.h, n_steps, ch, lnl)
+        if not record:
+            return None, None
+        return ch.cpu().numpy(), lnl.cpu().numpy()
+
+    def run_device(self, n_steps, d_chain=None, d_lnl=None):
+        lisa_sampler_run(self.h, n_steps, d_chain, d_lnl)
+
+    def state(self):
+        x = np.empty((self.T, self.W, SAMPLER_NDIM))
+        lnl = np.empty((self.T, self.W))
+        betas = np.empty(self.T)
+        step = lisa_sampler_get_state(self.h, x, lnl, betas)
+        return x, lnl, betas, step
+
+    def counts(self):
+        acc = np.empty((self.T, 2), dtype=np.int64)
+        sw = np.empty((self.T, 2), dtype=np.int64)
+        lisa_sampler_get_counts(self.h, acc, sw)
+        return acc, sw
+
+    def step_launches(self):
+        return lisa_sampler_step_launches(self.h)
+
+
+def sky_mode_init(x_center, scale, lower, upper, T, W, seed):
+    out = np.empty((T, W, SAMPLER_NDIM))
+    lisa_sampler_sky_mode_init(x_center, scale, lower, upper, T, W, seed, out)
+    return out
+
+
+def autocorr_time(chain, stride=1, offset=0, return_rho=False):
+    """tau of Sec. III.C on the device; chain is a torch tensor or numpy array of shape
+    [n, W] (stride 1) or [n, W, stride]."""
+    import torch
+
+    t = chain if hasattr(chain, "data_ptr") else torch.as_tensor(np.ascontiguousarray(chain))
+    t = t.to(device="cuda", dtype=torch.float64).contiguous()
+    n, W = t.shape[0], t.shape[1]
+    rho = np.empty(n) if return_rho else None
+    torch.cuda.synchronize()
+    tau = lisa_autocorr_time(t, n, W, stride, offset, rho)
+    return (tau, rho) if return_rho else tau

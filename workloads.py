@@ -34,10 +34,11 @@ TABLE1_UPPER = np.array([math.log(1e9), 1.0, 0.99, 0.99, math.log(1298.0), 2 * m
                          2 * math.pi, 1.0, math.pi, math.log(3.15576e8)])
 
 # Parallel-tempered sampler workload: 8 temperatures x 256 walkers around an injection
-# with M_T = 2e6 Msun, q = 0.5, z = 3 (other parameters as Table II's Binary 1).
+# with M_T = 2e6 Msun, q = 0.5, z = 3 (angles as Table II's Binary 1; t_ref = 3600 s so
+# that the LISA-frame reference time, which differs by up to 500 s, stays positive).
 SAMPLER_T, SAMPLER_W = 8, 256
 THETA_SAMPLER_Z = (2e6, 0.5, 0.0, 0.0, 3.0, 2.14, 1.05, -0.024 % (2 * math.pi), 0.62, 2.03,
-                   50.25)
+                   3600.0)
 
 # Table II of the paper: Binary, M_T [Msun], q, a1, a2, D_L [Gpc], phi_ref, iota,
 # lambda, beta, psi, t_ref [s], SNR (the injections studied in Sec. IV).
