@@ -316,6 +316,183 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
                                                     "dense", "finish"), stage_ms)}}}
 
 
+SAMPLER_METRIC = "PT sampler steps/s (8 temps x 256 walkers, 6 modes, A/E/T, 1-yr df)"
+SAMPLER_WORKLOAD = ("parallel-tempered stretch-move sampler, 8 temperatures x 256 walkers "
+                    "(a=1.15, geometric ladder ratio 2.04807, hottest infinite, adaptive), "
+                    "LISA-frame sampling over the Table I prior, 8-sky-mode start; likelihood: "
+                    "6 modes, K=1024, 1-yr grid (3155445 bins), A/E/T; injection M_T=2e6 "
+                    "Msun, q=0.5, z=3 (SNR ~880) + seeded noise")
+
+
+def sampler_cpu_baseline(steps=4):
+    """The oracle sampler as it stands on a bounded sample: 2 temperatures x 8 walkers of
+    the same workload for a few steps (each step = 16 oracle ln L evaluations)."""
+    import oracle
+
+    g = W.GRID_C2
+    S = oracle.psd_aet(g.freqs())
+    inj = np.array(W.THETA_SAMPLER_Z)
+    inj[4] = oracle.dl_gpc(inj[4])
+    d = oracle.template(inj, W.T0_YEAR, W.MODES6, 1024, g.f0, g.df, g.n_bins)
+    d = d + oracle.noise(S, g.df, W.white_noise(g.n_bins, 2))
+    xc = oracle.from_physical(inj)
+    tL, lamL, betL, psiL = oracle.ssb_to_lisa(inj[10] + W.T0_YEAR, inj[7], inj[8], inj[9])
+    xc[7], xc[8], xc[9], xc[10] = lamL, math.sin(betL), psiL, math.log(tL - W.T0_YEAR)
+    x0 = xc + 1e-4 * np.random.default_rng(1).standard_normal((2, 8, 11))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.sampler_lisa(x0, [1.0, 0.5], steps, 1, W.TABLE1_LOWER, W.TABLE1_UPPER, W.T0_YEAR,
+                        W.MODES6, 1024, g.f0, g.df, d, S, n_threads=threads)
+    dt = time.perf_counter() - t0
+    evals = 16 * (steps + 1)
+    return {"value": evals / dt, "unit": "ln L evals/s inside the sampler", "cores": threads,
+            "kind": "oracle",
+            "sample": "2 temperatures x 8 walkers, %d steps plus the initial evaluation" % steps,
+            "steps_per_s_full_ensemble": evals / dt / (W.SAMPLER_T * W.SAMPLER_W),
+            "seconds": dt}
+
+
+def run_sampler(args, world, rank, local):
+    """The sampler workload: K timed steps after W warm-up (burn-in) steps; value =
+    sampler steps per second of the whole job (each step evaluates every walker once)."""
+    import torch
+
+    from paper_2005_01827_gb300 import LisaLike, build, lisalike as LL
+
+    build.build()
+    torch.cuda.set_device(local)
+    T, Wk = W.SAMPLER_T, W.SAMPLER_W
+    g = W.GRID_C2
+    prec = LL.LISA_PREC_SPLIT if args.precision == "split" else LL.LISA_PREC_FP64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=T * Wk // 2,
+                    device=local, precision=prec, stream=stream.cuda_stream)
+    psd = np.empty((3, g.n_bins))
+    LL.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
+    like.set_data(g.f0, g.df, g.n_bins, None, psd)
+    inj = np.array(W.THETA_SAMPLER_Z)
+    inj[4] = LL.lisa_dl_from_z(inj[4])
+    h = like.template(inj)
+    z = W.white_noise(g.n_bins, 2)
+    d = h + 0.5 * np.sqrt(psd / g.df) * (z[..., 0] + 1j * z[..., 1])
+    like.set_data(g.f0, g.df, g.n_bins, d, psd)
+    cfg = LL.lisa_sampler_default_config()
+    xc = LL.from_physical(inj, True, W.T0_YEAR)
+    scale = np.array([1e-3, 1e-3, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2, 1e-3, 1e-3, 1e-2, 1e-4])
+    x0 = LL.sky_mode_init(xc, scale, list(cfg.lower), list(cfg.upper), T, Wk, 7 + rank)
+    # tile shapes from the autotuner, timed on the starting walkers
+    dx = torch.tensor(x0.reshape(-1, 11)[: T * Wk // 2], dtype=torch.float64, device="cuda")
+    dth = torch.empty_like(dx)
+    LL.lisa_sampler_to_physical(dx, dx.shape[0], True, W.T0_YEAR, dth, stream.cuda_stream)
+    stream.synchronize()
+    th_start = dth.cpu().numpy()
+    LL.lisa_like_autotune(like.h, th_start[:256], 256)
+    s = LL.LisaSampler(like, seed=11 + rank)
+    s.set_state(x0)
+    s.run(max(args.warmup, 3), record=False)          # burn-in; also captures the graph
+    K = args.steps
+    chain = torch.empty((K, Wk, 11), dtype=torch.float64, device="cuda")
+    lch = torch.empty((K, Wk), dtype=torch.float64, device="cuda")
+    acc0, sw0 = s.counts()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.run_device(K, chain, lch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    acc1, sw1 = s.counts()
+    launches = K * s.step_launches()
+    xs, lnls, betas, step = s.state()
+    taus = [LL.lisa_autocorr_time(chain, K, Wk, 11, q, None, stream.cuda_stream)
+            for q in range(11)]
+    tau = float(np.nanmax(taus))
+    sec = ms * 1e-3
+    value = world * K / sec
+    ess = K * Wk / tau
+    # the likelihood inside a step: one profiled call on the current proposals' batch
+    # size, with the current walkers of every temperature (half of them)
+    dx = torch.tensor(xs.reshape(-1, 11)[: T * Wk // 2], dtype=torch.float64, device="cuda")
+    LL.lisa_sampler_to_physical(dx, dx.shape[0], True, W.T0_YEAR, dth, stream.cuda_stream)
+    stream.synchronize()
+    thn = dth.cpu().numpy()
+    lnl_b = torch.empty(T * Wk // 2, dtype=torch.float64, device="cuda")
+
+    def like_call():
+        LL.lisa_like_loglike_device(like.h, dth, T * Wk // 2, lnl_b, None, None,
+                                    stream.cuda_stream)
+
+    like_call()
+    stage_ms, ncalls = profile_once(LL, like, like_call)
+    mode_bins, bins = work_units(like, thn)
+    dense_ms = stage_ms[4] / max(ncalls, 1)
+    flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
+    achieved = flops / (dense_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops() if prec == LL.LISA_PREC_SPLIT else fp64_peak_tflops()
+    like_ms = sum(stage_ms) / max(ncalls, 1)
+    # sampler kernels alone: the same ensemble on the Gaussian target
+    gs = LL.LisaSampler(None, n_temps=T, n_walkers=Wk, target=LL.LISA_TARGET_GAUSSIAN,
+                        lisa_frame=1, seed=3)
+    gs.set_state(x0)
+    gs.run(3, record=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs.run(200, record=False)
+    own_ms = (time.perf_counter() - t0) * 1e3 / 200
+    gs.close()
+    # end to end through the public host API: state upload, K steps, chain download
+    t0 = time.perf_counter()
+    s.set_state(xs, step)
+    c_host, l_host = s.run(K)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * K / e2e_s, "unit": "steps/s",
+           "h2d_bytes_per_step": T * Wk * 11 * 8 / K,
+           "d2h_bytes_per_step": Wk * 12 * 8}
+    s.close()
+    like.close()
+    line = {"metric": SAMPLER_METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == LL.LISA_PREC_SPLIT else "f64", "data": "synthetic",
+            "config": {"workload": SAMPLER_WORKLOAD, "temps": T, "walkers_per_temp": Wk,
+                       "precision": args.precision, "graphs": True,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (data 227 MB, spline coefficients 0.8 GB)"},
+            "evals_per_s": value * T * Wk,
+            "mcmc": {"tau_max": tau, "tau": taus, "chain_steps": K,
+                     "chain_over_tau": K / tau, "ess": ess, "ess_per_s": world * ess / sec,
+                     "acceptance": ((acc1 - acc0)[:, 0] / np.maximum((acc1 - acc0)[:, 1], 1)).tolist(),
+                     "swap_acceptance": ((sw1 - sw0)[:-1, 0] / np.maximum((sw1 - sw0)[:-1, 1], 1)).tolist(),
+                     "betas": betas.tolist(),
+                     "note": "tau from a chain shorter than 50 tau is a lower bound"},
+            "step_breakdown_ms": {"likelihood_per_call": like_ms, "likelihood_calls": 2,
+                                  "sampler_kernels_per_step": own_ms},
+            "roofline": {"bound": "alu", "kernel": "dense_split_kernel" if prec == LL.LISA_PREC_SPLIT
+                         else "dense_f64_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "note": "one profiled likelihood call on the sampler's batch of %d "
+                                 "walkers after the timed steps" % (T * Wk // 2),
+                         "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
+                                               zip(("knots", "splines", "segprep", "plan",
+                                                    "dense", "finish"), stage_ms)}},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = sampler_cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
 def profile_once(lisalike, like, step):
     """Per-stage CUDA-event times of one call (profiling off afterwards)."""
     lisalike.lisa_like_set_profiling(like.h, True)
@@ -338,13 +515,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true",
                     help="skip the split-precision timing of the same workload")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "sampler"],
                     help="c2: the 1024-walker benchmark workload; c3: 8192 walkers with "
-                         "masses 1e3..1e9 Msun under CUDA-graph replay with autotuned tiles")
+                         "masses 1e3..1e9 Msun under CUDA-graph replay with autotuned tiles; "
+                         "sampler: the parallel-tempered ensemble sampler on the likelihood")
+    ap.add_argument("--precision", default="split", choices=["split", "fp64"],
+                    help="likelihood precision of the sampler workload")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "sampler":
+        return run_sampler(args, world, rank, local)
 
     import torch
 

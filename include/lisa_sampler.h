@@ -123,6 +123,14 @@ const char *lisa_sampler_last_error(const lisa_sampler_t *s);
 lisa_status lisa_sampler_to_physical(const double *d_x, int n, int lisa_frame, double t0,
                                      double *d_th, void *stream);
 
+/* The inverse on the host: physical parameters th [n][11] (SSB frame, t_ref relative to
+ * t0) -> sampling coordinates x [n][11], with lambda, sin beta, psi and ln t_ref in the
+ * LISA frame when lisa_frame (t_L = t + k . p0(t), then the constellation frame at t_L).
+ * LISA_ERR_ARG when a parameter has no sampling coordinate (M_T, D_L or the reference
+ * time not positive). */
+lisa_status lisa_sampler_from_physical(const double *th, int n, int lisa_frame, double t0,
+                                       double *x);
+
 /* Initial walkers at the 8 LISA-frame sky modes of Sec. III.B: walker w of every
  * temperature sits at mode w % 8, longitude lambda_L + (w % 4) pi/2 (wrapped into the
  * prior range) and sin beta_L with sign flipped for (w / 4) % 2 = 1, plus a Gaussian

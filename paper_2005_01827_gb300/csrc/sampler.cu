@@ -782,6 +782,68 @@ lisa_status lisa_sampler_to_physical(const double *d_x, int n, int lisa_frame, d
     return LISA_OK;
 }
 
+lisa_status lisa_sampler_from_physical(const double *th, int n, int lisa_frame, double t0,
+                                       double *x) {
+    lisa::set_thread_error("");
+    if (!th || !x || n < 0 || !std::isfinite(t0)) {
+        lisa::set_thread_error("NULL pointer, negative n or non-finite t0");
+        return LISA_ERR_ARG;
+    }
+    for (int i = 0; i < n; i++) {
+        const double *p = th + (size_t)i * D;
+        double *o = x + (size_t)i * D;
+        if (!(p[0] > 0.0) || !(p[4] > 0.0)) {
+            lisa::set_thread_error("M_T and D_L must be positive");
+            return LISA_ERR_ARG;
+        }
+        o[0] = std::log(p[0]);
+        o[1] = p[1];
+        o[2] = p[2];
+        o[3] = p[3];
+        o[4] = std::log(p[4]);
+        o[5] = p[5];
+        o[6] = std::cos(p[6]);
+        double lam = p[7], sb = std::sin(p[8]), psi = p[9], tref = p[10];
+        if (lisa_frame) {
+            const double cl = std::cos(p[7]), sl = std::sin(p[7]), cb = std::cos(p[8]);
+            const double cp = std::cos(p[9]), sp = std::sin(p[9]);
+            const double nv[3] = {cb * cl, cb * sl, sb};
+            const double pv[3] = {cp * sl - sp * sb * cl, -cp * cl - sp * sb * sl, sp * cb};
+            const double t = p[10] + t0;
+            const double al = 2.0 * kPi * t / kYearS;
+            const double tL = t - kAuS * (nv[0] * std::cos(al) + nv[1] * std::sin(al));
+            const double a2 = 2.0 * kPi * tL / kYearS, ca = std::cos(a2), sa = std::sin(a2);
+            const double h = 0.8660254037844386467637231707529362;
+            const double Q[3][3] = {{0.5 * ca * ca + sa * sa, -0.5 * ca * sa, -h * ca},
+                                    {-0.5 * ca * sa, 0.5 * sa * sa + ca * ca, -h * sa},
+                                    {h * ca, h * sa, 0.5}};
+            double nL[3], pL[3];
+            for (int r = 0; r < 3; r++) {  // Q^T: constellation frame components
+                nL[r] = Q[0][r] * nv[0] + Q[1][r] * nv[1] + Q[2][r] * nv[2];
+                pL[r] = Q[0][r] * pv[0] + Q[1][r] * pv[1] + Q[2][r] * pv[2];
+            }
+            lam = std::atan2(nL[1], nL[0]);
+            if (lam < 0.0) lam += 2.0 * kPi;
+            sb = std::fmin(1.0, std::fmax(-1.0, nL[2]));
+            const double rho2 = nL[0] * nL[0] + nL[1] * nL[1];
+            psi = std::atan2(-sb * (pL[0] * nL[0] + pL[1] * nL[1]) + pL[2] * rho2,
+                             pL[0] * nL[1] - pL[1] * nL[0]);
+            psi = std::fmod(psi, kPi);
+            if (psi < 0.0) psi += kPi;
+            tref = tL - t0;
+        }
+        if (!(tref > 0.0)) {
+            lisa::set_thread_error("the reference time must be positive in the sampling frame");
+            return LISA_ERR_ARG;
+        }
+        o[7] = lam;
+        o[8] = sb;
+        o[9] = psi;
+        o[10] = std::log(tref);
+    }
+    return LISA_OK;
+}
+
 lisa_status lisa_sampler_sky_mode_init(const double *xc, const double *scale, const double *lower,
                                        const double *upper, int T, int W, uint64_t seed,
                                        double *x_out) {

@@ -35,7 +35,8 @@ SYMBOLS = (
     "lisa_sampler_default_config", "lisa_sampler_create", "lisa_sampler_set_ladder",
     "lisa_sampler_set_state", "lisa_sampler_run", "lisa_sampler_get_state",
     "lisa_sampler_get_counts", "lisa_sampler_step_launches", "lisa_sampler_destroy",
-    "lisa_sampler_last_error", "lisa_sampler_to_physical", "lisa_sampler_sky_mode_init",
+    "lisa_sampler_last_error", "lisa_sampler_to_physical", "lisa_sampler_from_physical",
+    "lisa_sampler_sky_mode_init",
     "lisa_autocorr_time",
 )
 LISA_TARGET_LIKELIHOOD, LISA_TARGET_GAUSSIAN = 0, 1
@@ -162,12 +163,13 @@ def load(path: str = LIB_PATH):
     L.lisa_sampler_last_error.argtypes = [vp]
     L.lisa_sampler_last_error.restype = C.c_char_p
     L.lisa_sampler_to_physical.argtypes = [vp, i, i, d, vp, vp]
+    L.lisa_sampler_from_physical.argtypes = [vp, i, i, d, vp]
     L.lisa_sampler_sky_mode_init.argtypes = [vp, vp, vp, vp, i, i, u64, vp]
     L.lisa_autocorr_time.argtypes = [vp, i, i, i, i, dp, vp, vp]
     for fn in ("lisa_sampler_create", "lisa_sampler_set_ladder", "lisa_sampler_set_state",
                "lisa_sampler_run", "lisa_sampler_get_state", "lisa_sampler_get_counts",
                "lisa_sampler_step_launches", "lisa_sampler_to_physical",
-               "lisa_sampler_sky_mode_init", "lisa_autocorr_time"):
+               "lisa_sampler_sky_mode_init", "lisa_autocorr_time", "lisa_sampler_from_physical"):
         getattr(L, fn).restype = i
     _lib = L
     return L
@@ -464,6 +466,20 @@ def lisa_sampler_to_physical(d_x, n, lisa_frame, t0, d_th, stream=None):
                                             _ptr(d_th), st))
 
 
+def lisa_sampler_from_physical(th, n, lisa_frame, t0, x_out):
+    t = _f64(th)
+    _scheck(load().lisa_sampler_from_physical(_ptr(t), int(n), int(bool(lisa_frame)), float(t0),
+                                              _ptr(x_out)))
+
+
+def from_physical(th, lisa_frame=True, t0=3.15576e7):
+    """Sampling coordinates of Table I (host) from physical parameters [n, 11] or [11]."""
+    t = _f64(np.atleast_2d(th))
+    out = np.empty_like(t)
+    lisa_sampler_from_physical(t, t.shape[0], lisa_frame, t0, out)
+    return out if np.ndim(th) == 2 else out[0]
+
+
 def lisa_sampler_sky_mode_init(x_center, scale, lower, upper, T, W, seed, x_out):
     xc, sc, lo, hi = _f64(x_center), _f64(scale), _f64(lower), _f64(upper)
     _scheck(load().lisa_sampler_sky_mode_init(_ptr(xc), _ptr(sc), _ptr(lo), _ptr(hi), int(T),
@@ -553,6 +569,21 @@ class LisaSampler:
 
     def step_launches(self):
         return lisa_sampler_step_launches(self.h)
+
+    def checkpoint(self, path):
+        """Save what a resumed run needs (walkers, ladder, next step counter, seed) to an
+        .npz file; ln L is re-evaluated on restore."""
+        x, _, betas, step = self.state()
+        np.savez(path, x=x, betas=betas, step=np.uint32(step), seed=np.uint64(self.cfg.seed))
+
+    def restore(self, path):
+        """Continue from a checkpoint: the next steps draw the same random numbers as the
+        uninterrupted run (counter-based generator keyed by the seed and the step)."""
+        z = np.load(path)
+        if int(z["seed"]) != int(self.cfg.seed):
+            raise ValueError("checkpoint was written by a sampler with another seed")
+        self.set_ladder(z["betas"])
+        self.set_state(z["x"], int(z["step"]))
 
 
 def sky_mode_init(x_center, scale, lower, upper, T, W, seed):

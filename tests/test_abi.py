@@ -92,3 +92,42 @@ def test_host_helpers(lib, orc):
     out = lisalike.psd_aet(f0, df, n)
     ref = orc.psd_aet(f0 + df * np.arange(n))
     assert np.allclose(out, ref, rtol=1e-12, atol=0)
+
+
+def test_sampler_host_functions_match_the_oracle(lib, orc):
+    """Host-only entry points of include/lisa_sampler.h, callable without a GPU."""
+    import math
+
+    import workloads as W
+    from paper_2005_01827_gb300 import lisalike as LL
+
+    rng = np.random.default_rng(3)
+    th = W.draw_walkers(64, 4, (3.0, 9.0))
+    th[:, 4] = rng.uniform(0.1, 100.0, 64)
+    th[:, 10] = rng.uniform(600.0, 1e7, 64)
+    for frame in (False, True):
+        x = LL.from_physical(th, frame, W.T0_YEAR)
+        for v, t in zip(x, th):
+            ref = orc.from_physical(t)
+            if frame:
+                tL, lamL, betL, psiL = orc.ssb_to_lisa(t[10] + W.T0_YEAR, t[7], t[8], t[9])
+                ref[7], ref[8], ref[9], ref[10] = lamL, math.sin(betL), psiL, math.log(tL - W.T0_YEAR)
+            d = np.abs(v - ref)
+            d[7] = abs((v[7] - ref[7] + math.pi) % (2 * math.pi) - math.pi)
+            d[9] = abs((v[9] - ref[9] + math.pi / 2) % math.pi - math.pi / 2)
+            assert np.max(d) <= 1e-11, (frame, d)
+    with pytest.raises(LL.LisaError):
+        LL.from_physical(np.where(np.arange(11) == 0, -1.0, th[0]), False, 0.0)
+    # sky-mode initialisation: 8 modes, W/8 walkers each, inside the prior box
+    c = LL.lisa_sampler_default_config()
+    lo, hi = np.array(list(c.lower)), np.array(list(c.upper))
+    xc = LL.from_physical(th[0], True, W.T0_YEAR)
+    x0 = LL.sky_mode_init(xc, np.full(11, 1e-6), lo, hi, 3, 32, 9)
+    assert np.all(x0 >= lo) and np.all(x0 <= hi)
+    for w in range(32):
+        lam = (xc[7] + (w % 4) * math.pi / 2 - lo[7]) % (hi[7] - lo[7]) + lo[7]
+        assert abs((x0[1, w, 7] - lam + math.pi) % (2 * math.pi) - math.pi) <= 1e-4
+        assert abs(x0[1, w, 8] - (xc[8] if w % 8 < 4 else -xc[8])) <= 1e-4
+    assert not np.array_equal(x0[0], x0[1])           # independent jitter per temperature
+    with pytest.raises(LL.LisaError):
+        LL.sky_mode_init(xc, np.full(11, 1e-6), lo, hi, 1, 12, 9)   # W not a multiple of 8

@@ -249,3 +249,29 @@ def test_sampler_workload_full_size(pkg, orc):
     assert np.all(err <= 1e-6)
     # the coldest walkers at the true sky mode sit near the injection's ln L
     assert np.max(lnl[0]) > -0.5 * dd + 0.5 * 880.0 ** 2 * 0.5
+
+
+def test_checkpoint_resume_continues_the_same_chain(pkg, tmp_path):
+    """Checkpoint/resume: 40 steps, save, a new sampler restores and runs 60 more; the
+    chain equals 100 uninterrupted steps (the ladder adapts throughout)."""
+    T, Wk = 3, 16
+    rng = np.random.default_rng(8)
+    x0 = MEAN + SIGMA * rng.standard_normal((T, Wk, D))
+    s = gauss_sampler(pkg, T, Wk, True, True, seed=21)
+    s.set_state(x0)
+    full, _ = s.run(100)
+    xf, _, bf, _ = s.state()
+    s.close()
+    s = gauss_sampler(pkg, T, Wk, True, True, seed=21)
+    s.set_state(x0)
+    a, _ = s.run(40)
+    s.checkpoint(tmp_path / "ck.npz")
+    s.close()
+    s = gauss_sampler(pkg, T, Wk, False, True, seed=21)
+    s.restore(tmp_path / "ck.npz")
+    b, _ = s.run(60)
+    xr, _, br, step = s.state()
+    s.close()
+    assert step == 100
+    assert np.array_equal(np.concatenate([a, b]), full)
+    assert np.array_equal(xr, xf) and np.array_equal(br, bf)
