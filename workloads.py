@@ -119,3 +119,24 @@ def near_injection(theta: np.ndarray, B: int, seed: int, scale: float = 1e-4) ->
     th[:, 1] = np.minimum(th[:, 1], 1.0)
     th[:, 2:4] = np.clip(th[:, 2:4], -0.99, 0.99)
     return th
+
+
+# Normalizing-flow proposal: 8 affine couplings over the 11 sampling coordinates, each
+# with a 2 x 128 hidden-layer network (11 -> 128 -> 128 -> 22).
+FLOW_COUPLINGS, FLOW_HIDDEN, FLOW_DIM = 8, 128, 11
+
+
+def flow_init_weights(seed: int, out_scale: float = 0.0) -> dict:
+    """Random starting weights of the flow (uniform +-sqrt(6/fan_in) for the hidden
+    layers, zero biases; the output layer scaled by ``out_scale``, 0 = identity flow)."""
+    rng = np.random.default_rng(seed)
+    C, H, D = FLOW_COUPLINGS, FLOW_HIDDEN, FLOW_DIM
+    lim1, lim2, lim3 = math.sqrt(6.0 / D), math.sqrt(6.0 / H), math.sqrt(6.0 / H)
+    return {
+        "W1": rng.uniform(-lim1, lim1, (C, H, D)).astype(np.float32),
+        "b1": np.zeros((C, H), np.float32),
+        "W2": rng.uniform(-lim2, lim2, (C, H, H)).astype(np.float32),
+        "b2": np.zeros((C, H), np.float32),
+        "W3": (out_scale * rng.uniform(-lim3, lim3, (C, 2 * D, H))).astype(np.float32),
+        "b3": (out_scale * rng.uniform(-0.1, 0.1, (C, 2 * D))).astype(np.float32),
+    }
