@@ -41,6 +41,7 @@
 
 #include <stdint.h>
 
+#include "lisa_flow.h"
 #include "lisa_like.h"
 
 #ifdef __cplusplus
@@ -115,6 +116,43 @@ int lisa_sampler_step_launches(const lisa_sampler_t *s);
 
 void lisa_sampler_destroy(lisa_sampler_t *s);
 const char *lisa_sampler_last_error(const lisa_sampler_t *s);
+
+/* Flow proposal (lisa_flow.h) for the coldest temperature.  Once active, every step
+ * starts with one independence Metropolis-Hastings move of each coldest walker
+ * (Eq. (13)): y = flow(z), z from Philox counters (step, 3, blk, w), blk = 0..2, by
+ * Box-Muller in pairs (the first 11 of 12 normals); accepted with probability
+ * min(1, [L(y)/L(x)]^beta_0 pi(y)/pi(x) q(x)/q(y)), the uniform from counter
+ * (step, 4, 0, w); the batched ln L of the W proposals runs inside the step's graph.
+ * Training: after every train_every steps (counted from set_state) the flow is fitted
+ * to the coldest walkers of those steps (lisa_flow_train: train_iters Adam steps on
+ * minibatches of `batch` rows, round = number of earlier trainings, key = seed); the
+ * proposals start after the first training.  No training after freeze_after steps
+ * (0: never stop); train_every = 0: never train, the flow's current weights propose
+ * from the first step (set them through lisa_sampler_get_flow).  flow_only = 1 skips the
+ * stretch moves and temperature swaps. */
+typedef struct {
+    int train_every;   /* 500 */
+    int train_iters;   /* 400 */
+    int batch;         /* 1024, a multiple of 64 */
+    double lr;         /* 1e-3 */
+    int freeze_after;  /* 0 */
+    uint64_t seed;     /* weight initialisation and minibatch draws: 1 */
+    int flow_only;     /* 0 */
+} lisa_flow_schedule;
+
+void lisa_flow_default_schedule(lisa_flow_schedule *fs);
+
+/* Enable the flow (once per sampler; the likelihood's max_batch must be >= W).
+ * Counters and the training schedule restart at the next set_state. */
+lisa_status lisa_sampler_enable_flow(lisa_sampler_t *s, const lisa_flow_schedule *fs);
+
+/* The sampler's flow (borrowed; NULL before lisa_sampler_enable_flow). */
+lisa_flow_t *lisa_sampler_get_flow(lisa_sampler_t *s);
+
+/* acc [2] = (accepted, proposed) flow moves since set_state; trainings so far; the last
+ * minibatch loss of the last training (NaN before the first).  Any may be NULL. */
+lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings,
+                                    double *last_loss);
 
 /* Sampling coordinates -> the physical parameter vector of lisa_like.h, on the device:
  * d_x [n][11] -> d_th [n][11], with the LISA-frame conversion when lisa_frame, absolute

@@ -14,56 +14,17 @@
 #include <vector>
 
 #include "../../include/lisa_sampler.h"
+#include "flow.h"
 #include "internal.h"
+#include "sampler_dev.cuh"
+
+using namespace lisa_smp;
 
 namespace {
 
-constexpr int D = LISA_SAMPLER_NDIM;
-constexpr int kMaxT = LISA_SAMPLER_MAX_TEMPS;
 constexpr int kThreads = 128;
 constexpr int kSwapThreads = 256;
-constexpr double kPi = 3.141592653589793238462643383279502884;
-constexpr double kYearS = 3.15576e7;                  // orbital period of the constellation
-constexpr double kAuS = 1.495978707e11 / 299792458.0;  // 1 AU in light seconds
-
-// ------------------------------------------------------------------ Philox4x32-10
-// Counter-based generator of Salmon, Moraes, Dror & Shaw (2011): ten rounds of two
-// 32x32 -> 64-bit products with the Weyl key schedule.
-__host__ __device__ inline uint32_t mulhi32(uint32_t a, uint32_t b) {
-#ifdef __CUDA_ARCH__
-    return __umulhi(a, b);
-#else
-    return (uint32_t)(((uint64_t)a * b) >> 32);
-#endif
-}
-
-struct U4 {
-    uint32_t v[4];
-};
-
-__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                     uint32_t k0, uint32_t k1) {
-    for (int r = 0; r < 10; r++) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = mulhi32(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = mulhi32(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    U4 o;
-    o.v[0] = c0;
-    o.v[1] = c1;
-    o.v[2] = c2;
-    o.v[3] = c3;
-    return o;
-}
-
-// uniform in (0, 1): (u + 1/2) 2^-32, exact in FP64
-__host__ __device__ inline double unit(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
+constexpr int kMaxT = LISA_SAMPLER_MAX_TEMPS;
 
 // ------------------------------------------------------------------ device state
 struct RecCtl {
@@ -85,97 +46,9 @@ struct Dev {
     int *err;                            // sticky: a likelihood call gave up
     const int *like_err;                 // the likelihood's flag of its last call (or NULL)
     RecCtl *rec;
+    double *ring;                        // [R][W][D] recent coldest states (flow training) or NULL
+    int ring_rows;                       // R
 };
-
-__device__ inline double ln_prior(const double *x, const Dev &s) {
-    for (int q = 0; q < D; q++)
-        if (!(x[q] >= s.lo[q] && x[q] <= s.hi[q])) return -INFINITY;
-    return 0.0;
-}
-
-// Gaussian test target, every operation rounded as written
-__device__ inline double gauss_lnl(const double *x, const Dev &s) {
-    double acc = 0.0;
-    for (int q = 0; q < D; q++) {
-        const double r = __ddiv_rn(__dsub_rn(x[q], s.mean[q]), s.sig[q]);
-        acc = __dadd_rn(acc, __dmul_rn(r, r));
-    }
-    return __dmul_rn(-0.5, acc);
-}
-
-// LISA frame -> SSB frame.  The constellation of the response model is a fixed triangle
-// rotated by Q = Rz(alpha) Ry(-pi/3) Rz(-alpha), alpha = 2 pi t / yr; the LISA frame is
-// the one in which the triangle is at rest, at the arrival time t_L (absolute seconds).
-__device__ inline void lisa_to_ssb(double tL, double lamL, double betL, double psiL, double *t,
-                                   double *lam, double *bet, double *psi) {
-    double sa, ca;
-    sincos(2.0 * kPi * tL / kYearS, &sa, &ca);
-    const double h = 0.8660254037844386467637231707529362;  // sqrt(3)/2
-    const double Q[3][3] = {{0.5 * ca * ca + sa * sa, -0.5 * ca * sa, -h * ca},
-                            {-0.5 * ca * sa, 0.5 * sa * sa + ca * ca, -h * sa},
-                            {h * ca, h * sa, 0.5}};
-    double sl, cl, sb, cb, sp, cp;
-    sincos(lamL, &sl, &cl);
-    sincos(betL, &sb, &cb);
-    sincos(psiL, &sp, &cp);
-    // direction to the source and polarisation axis cos(psi) u + sin(psi) v in the L frame
-    const double nL[3] = {cb * cl, cb * sl, sb};
-    const double pL[3] = {cp * sl - sp * sb * cl, -cp * cl - sp * sb * sl, sp * cb};
-    double n[3], p[3];
-    for (int i = 0; i < 3; i++) {
-        n[i] = Q[i][0] * nL[0] + Q[i][1] * nL[1] + Q[i][2] * nL[2];
-        p[i] = Q[i][0] * pL[0] + Q[i][1] * pL[1] + Q[i][2] * pL[2];
-    }
-    double l = atan2(n[1], n[0]);
-    if (l < 0.0) l += 2.0 * kPi;
-    const double nz = fmin(1.0, fmax(-1.0, n[2]));
-    // u = (n_y, -n_x, 0)/rho and v = (-n_z n_x, -n_z n_y, rho^2)/rho with rho = cos(beta)
-    const double rho2 = n[0] * n[0] + n[1] * n[1];
-    double ps = atan2(-nz * (p[0] * n[0] + p[1] * n[1]) + p[2] * rho2, p[0] * n[1] - p[1] * n[0]);
-    ps = fmod(ps, kPi);
-    if (ps < 0.0) ps += kPi;
-    // arrival at the centre t_L = t + k . p0(t) with k = -n: fixed point in t
-    double tt = tL;
-    for (int it = 0; it < 6; it++) {
-        double s2, c2;
-        sincos(2.0 * kPi * tt / kYearS, &s2, &c2);
-        tt = tL + kAuS * (n[0] * c2 + n[1] * s2);
-    }
-    *t = tt;
-    *lam = l;
-    *bet = asin(nz);
-    *psi = ps;
-}
-
-// sampling coordinates of Table I -> physical parameters of the likelihood
-__device__ inline void to_physical(const double *x, int lisa_frame, double t0, double *th) {
-    th[0] = exp(x[0]);
-    th[1] = x[1];
-    th[2] = x[2];
-    th[3] = x[3];
-    th[4] = exp(x[4]);
-    th[5] = x[5];
-    th[6] = acos(x[6]);
-    if (lisa_frame) {
-        double t, l, b, p;
-        lisa_to_ssb(exp(x[10]) + t0, x[7], asin(x[8]), x[9], &t, &l, &b, &p);
-        th[7] = l;
-        th[8] = b;
-        th[9] = p;
-        th[10] = t - t0;
-    } else {
-        th[7] = x[7];
-        th[8] = asin(x[8]);
-        th[9] = x[9];
-        th[10] = exp(x[10]);
-    }
-}
-
-// parameters the likelihood rejects (lnL = -inf, no dense work)
-__device__ inline void invalid_params(double *th) {
-    th[0] = __longlong_as_double(0x7ff8000000000000LL);
-    for (int q = 1; q < D; q++) th[q] = 0.0;
-}
 
 // ------------------------------------------------------------------ kernels
 // ln pi and the likelihood input (or the Gaussian ln L) of walkers c*T*H .. (c+1)*T*H-1
@@ -184,10 +57,10 @@ __global__ void init_kernel(Dev s, int c) {
     if (p >= s.T * s.H) return;
     const int i = c * s.T * s.H + p;
     const double *x = s.x + (size_t)i * D;
-    const double lp = ln_prior(x, s);
+    const double lp = ln_prior(x, s.lo, s.hi);
     s.lnp[i] = lp;
     if (s.target == LISA_TARGET_GAUSSIAN) {
-        s.lnl[i] = gauss_lnl(x, s);
+        s.lnl[i] = gauss_lnl(x, s.mean, s.sig);
     } else if (isfinite(lp)) {
         to_physical(x, s.lisa_frame, s.t0, s.pth + (size_t)p * D);
     } else {
@@ -211,13 +84,13 @@ __global__ void propose_kernel(Dev s, int h) {
     const double *xj = s.x + ((size_t)t * s.W + j) * D;
     double y[D];
     for (int q = 0; q < D; q++) y[q] = __dadd_rn(xj[q], __dmul_rn(z, __dsub_rn(xk[q], xj[q])));
-    const double lp = ln_prior(y, s);
+    const double lp = ln_prior(y, s.lo, s.hi);
     double *yo = s.y + (size_t)p * D;
     for (int q = 0; q < D; q++) yo[q] = y[q];
     s.z[p] = z;
     s.py[p] = lp;
     if (s.target == LISA_TARGET_GAUSSIAN)
-        s.ly[p] = gauss_lnl(y, s);
+        s.ly[p] = gauss_lnl(y, s.mean, s.sig);
     else if (isfinite(lp))
         to_physical(y, s.lisa_frame, s.t0, s.pth + (size_t)p * D);
     else
@@ -283,6 +156,10 @@ __global__ void __launch_bounds__(kSwapThreads) swap_kernel(Dev s) {
     __syncthreads();
     RecCtl *rc = s.rec;
     const int row = rc->i;
+    if (s.ring) {
+        double *dst = s.ring + (size_t)(step % (unsigned)s.ring_rows) * s.W * D;
+        for (int i = tid; i < s.W * D; i += blockDim.x) dst[i] = s.x[i];
+    }
     if (rc->chain || rc->lnl) {
         for (int w = tid; w < s.W; w += blockDim.x) {
             if (rc->chain)
@@ -388,6 +265,17 @@ struct lisa_sampler {
     cudaEvent_t done = nullptr;
     std::vector<void *> bufs;
     std::string err;
+    // flow proposal
+    lisa_flow_t *flow = nullptr;
+    lisa_flow_schedule fs{};
+    bool flow_on = false;        // enabled
+    bool flow_active = false;    // proposals are being made (trained or forced)
+    int trainings = 0;
+    int64_t since_train = 0;     // steps recorded in the ring since the last training
+    int64_t steps_run = 0;       // steps since set_state
+    lisa_flowint::FStep fst{};
+    cudaGraphExec_t gexec_flow = nullptr;
+    int g_launches_flow = 0;
 };
 
 namespace {
@@ -431,9 +319,27 @@ lisa_status wait_done(lisa_sampler_t *s, double limit_s) {
 }
 
 // the kernels of one step on the sampler's stream
-lisa_status enqueue_step(lisa_sampler_t *s, int *nl) {
+lisa_status enqueue_step(lisa_sampler_t *s, bool with_flow, int *nl) {
     const int n = s->dev.T * s->dev.H;
     int count = 0;
+    if (with_flow) {
+        SCK(lisa_flowint::launch_flow_propose(s->flow, s->fst, s->stream), "flow proposal launch");
+        count++;
+        if (s->dev.target == LISA_TARGET_LIKELIHOOD) {
+            int l = 0;
+            lisa_status st = lisa::like_enqueue(s->like, s->fst.fpth, s->fst.W, s->fst.fly, s->stream, &l);
+            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->like));
+            count += l;
+        }
+        SCK(lisa_flowint::launch_flow_accept(s->fst, s->stream), "flow acceptance launch");
+        count++;
+        if (s->fs.flow_only) {
+            swap_kernel<<<1, kSwapThreads, 0, s->stream>>>(s->dev);
+            SCK(cudaGetLastError(), "swap kernel launch");
+            *nl = count + 1;
+            return LISA_OK;
+        }
+    }
     for (int h = 0; h < 2; h++) {
         propose_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(s->dev, h);
         SCK(cudaGetLastError(), "proposal kernel launch");
@@ -457,28 +363,53 @@ lisa_status enqueue_step(lisa_sampler_t *s, int *nl) {
 
 void drop_graph(lisa_sampler_t *s) {
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->gexec_flow) cudaGraphExecDestroy(s->gexec_flow);
     s->gexec = nullptr;
+    s->gexec_flow = nullptr;
 }
 
-lisa_status capture(lisa_sampler_t *s) {
-    drop_graph(s);
+lisa_status capture_one(lisa_sampler_t *s, bool with_flow, cudaGraphExec_t *out, int *launches) {
     cudaGraph_t g = nullptr;
     SCK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
     int nl = 0;
-    lisa_status st = enqueue_step(s, &nl);
+    lisa_status st = enqueue_step(s, with_flow, &nl);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (st != LISA_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     if (e != cudaSuccess) return scuda(s, e, "graph capture");
-    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        s->gexec = nullptr;
+        *out = nullptr;
         return scuda(s, e, "graph instantiation");
     }
-    s->g_launches = nl;
+    *launches = nl;
+    return LISA_OK;
+}
+
+lisa_status capture(lisa_sampler_t *s) {
+    drop_graph(s);
+    lisa_status st = capture_one(s, false, &s->gexec, &s->g_launches);
+    if (st == LISA_OK && s->flow_on) st = capture_one(s, true, &s->gexec_flow, &s->g_launches_flow);
+    return st;
+}
+
+// steps [i0, i0 + k) with or without the flow proposal
+lisa_status launch_steps(lisa_sampler_t *s, int k, bool with_flow) {
+    if (s->cfg.use_graphs) {
+        cudaGraphExec_t ge = with_flow ? s->gexec_flow : s->gexec;
+        for (int i = 0; i < k; i++) SCK(cudaGraphLaunch(ge, s->stream), "cudaGraphLaunch");
+        s->launches = with_flow ? s->g_launches_flow : s->g_launches;
+    } else {
+        for (int i = 0; i < k; i++) {
+            int nl = 0;
+            lisa_status st = enqueue_step(s, with_flow, &nl);
+            if (st != LISA_OK) return st;
+            s->launches = nl;
+        }
+    }
     return LISA_OK;
 }
 
@@ -665,6 +596,8 @@ lisa_status lisa_sampler_set_state(lisa_sampler_t *s, const double *x, uint32_t 
     SCK(cudaMemsetAsync(d.acc, 0, sizeof(unsigned long long) * 2 * d.T, s->stream), "cudaMemsetAsync");
     SCK(cudaMemsetAsync(d.swaps, 0, sizeof(unsigned long long) * 2 * d.T, s->stream), "cudaMemsetAsync");
     SCK(cudaMemsetAsync(d.err, 0, sizeof(int), s->stream), "cudaMemsetAsync");
+    if (s->flow_on)
+        SCK(cudaMemsetAsync(s->fst.facc, 0, sizeof(unsigned long long) * 2, s->stream), "cudaMemsetAsync");
     const int n = d.T * d.H;
     for (int c = 0; c < 2; c++) {
         init_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(d, c);
@@ -684,6 +617,8 @@ lisa_status lisa_sampler_set_state(lisa_sampler_t *s, const double *x, uint32_t 
     lisa_status w = wait_done(s, s->timeout_s);
     if (w != LISA_OK) return w;
     s->have_state = true;
+    s->steps_run = 0;
+    s->since_train = 0;
     return LISA_OK;
 }
 
@@ -701,14 +636,30 @@ lisa_status lisa_sampler_run(lisa_sampler_t *s, int n_steps, double *d_chain, do
         // likelihood buffers can change with set_data or a new tile shape: capture afresh
         lisa_status st = capture(s);
         if (st != LISA_OK) return st;
-        for (int i = 0; i < n_steps; i++) SCK(cudaGraphLaunch(s->gexec, s->stream), "cudaGraphLaunch");
-        s->launches = s->g_launches;
-    } else {
-        for (int i = 0; i < n_steps; i++) {
-            int nl = 0;
-            lisa_status st = enqueue_step(s, &nl);
-            if (st != LISA_OK) return st;
-            s->launches = nl;
+    }
+    const bool may_train = s->flow_on && s->fs.train_every > 0;
+    for (int done = 0; done < n_steps;) {
+        int k = n_steps - done;
+        const bool frozen = s->fs.freeze_after > 0 && s->steps_run >= s->fs.freeze_after;
+        if (may_train && !frozen) {
+            const int64_t to_train = s->fs.train_every - s->since_train;
+            if (to_train > 0 && to_train < k) k = (int)to_train;
+        }
+        lisa_status st = launch_steps(s, k, s->flow_active);
+        if (st != LISA_OK) return st;
+        done += k;
+        s->steps_run += k;
+        s->since_train += k;
+        if (may_train && !frozen && s->since_train >= s->fs.train_every) {
+            // the ring holds the coldest walkers of the last train_every steps
+            st = lisa_flowint::flow_train_async(s->flow, s->dev.ring,
+                                                (int64_t)s->fs.train_every * s->dev.W,
+                                                s->fs.train_iters, s->fs.batch, s->fs.lr,
+                                                s->fs.seed, (uint32_t)s->trainings, s->stream);
+            if (st != LISA_OK) return sfail(s, st, std::string("flow training: ") + lisa_flow_last_error(s->flow));
+            s->trainings++;
+            s->since_train = 0;
+            s->flow_active = true;
         }
     }
     SCK(cudaMemcpyAsync(s->h_err, s->dev.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
@@ -748,11 +699,91 @@ lisa_status lisa_sampler_get_counts(lisa_sampler_t *s, int64_t *acc, int64_t *sw
 
 int lisa_sampler_step_launches(const lisa_sampler_t *s) { return s ? s->launches : 0; }
 
+void lisa_flow_default_schedule(lisa_flow_schedule *fs) {
+    if (!fs) return;
+    std::memset(fs, 0, sizeof(*fs));
+    fs->train_every = 500;
+    fs->train_iters = 400;
+    fs->batch = 1024;
+    fs->lr = 1e-3;
+    fs->freeze_after = 0;
+    fs->seed = 1;
+    fs->flow_only = 0;
+}
+
+lisa_status lisa_sampler_enable_flow(lisa_sampler_t *s, const lisa_flow_schedule *fs) {
+    if (!s) return LISA_ERR_ARG;
+    if (!fs) return sfail(s, LISA_ERR_ARG, "NULL schedule");
+    if (fs->train_every < 0 || (fs->train_every > 0 && (fs->train_iters < 1 || fs->batch < 64 ||
+                                                        fs->batch % 64 || !(fs->lr > 0.0))))
+        return sfail(s, LISA_ERR_ARG, "train_every >= 0; when training: iters >= 1, batch a multiple of 64, lr > 0");
+    if (s->flow_on) return sfail(s, LISA_ERR_STATE, "the flow is already enabled");
+    Dev &d = s->dev;
+    if (s->like && d.W > s->li.max_batch)
+        return sfail(s, LISA_ERR_ARG, "the likelihood's max_batch must be >= n_walkers for flow proposals");
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    lisa_status st = lisa_flow_create(fs->seed, &s->flow);
+    if (st != LISA_OK) return sfail(s, st, std::string("flow: ") + lisa_flow_last_error(nullptr));
+    const size_t W = d.W;
+    lisa_flowint::FStep &a = s->fst;
+    cudaError_t e;
+    if ((e = salloc(s, &a.fy, W * D)) != cudaSuccess || (e = salloc(s, &a.fpth, W * D)) != cudaSuccess ||
+        (e = salloc(s, &a.fly, W)) != cudaSuccess || (e = salloc(s, &a.fq, W)) != cudaSuccess ||
+        (e = salloc(s, &a.fpy, W)) != cudaSuccess || (e = salloc(s, &a.facc, 2)) != cudaSuccess)
+        return scuda(s, e, "device allocation (flow step)");
+    if (fs->train_every > 0) {
+        if ((e = salloc(s, &d.ring, (size_t)fs->train_every * W * D)) != cudaSuccess)
+            return scuda(s, e, "device allocation (training ring)");
+        d.ring_rows = fs->train_every;
+    }
+    SCK(cudaMemsetAsync(a.facc, 0, sizeof(unsigned long long) * 2, s->stream), "cudaMemsetAsync");
+    a.W = d.W;
+    a.k0 = d.k0;
+    a.k1 = d.k1;
+    a.step = d.step;
+    a.x = d.x;
+    a.lnl = d.lnl;
+    a.lnp = d.lnp;
+    a.betas = d.betas;
+    for (int q = 0; q < D; q++) {
+        a.lo[q] = d.lo[q];
+        a.hi[q] = d.hi[q];
+        a.mean[q] = d.mean[q];
+        a.sig[q] = d.sig[q];
+    }
+    a.lisa_frame = d.lisa_frame;
+    a.target = d.target;
+    a.t0 = d.t0;
+    a.err = d.err;
+    a.like_err = d.like_err;
+    s->fs = *fs;
+    s->flow_on = true;
+    s->flow_active = fs->train_every == 0;  // no training: the caller's weights propose at once
+    drop_graph(s);
+    return wait_done(s, s->timeout_s);
+}
+
+lisa_flow_t *lisa_sampler_get_flow(lisa_sampler_t *s) { return s ? s->flow : nullptr; }
+
+lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings, double *last_loss) {
+    if (!s) return LISA_ERR_ARG;
+    if (!s->flow_on) return sfail(s, LISA_ERR_STATE, "the flow is not enabled");
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (acc) SCK(cudaMemcpyAsync(acc, s->fst.facc, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s->stream), "download");
+    if (last_loss) {
+        lisa_status st = lisa_flowint::flow_last_loss(s->flow, last_loss, s->stream);
+        if (st != LISA_OK) return sfail(s, st, lisa_flow_last_error(s->flow));
+    }
+    if (trainings) *trainings = s->trainings;
+    return wait_done(s, s->timeout_s);
+}
+
 void lisa_sampler_destroy(lisa_sampler_t *s) {
     if (!s) return;
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     drop_graph(s);
+    if (s->flow) lisa_flow_destroy(s->flow);
     for (void *p : s->bufs) cudaFree(p);
     if (s->h_rec) cudaFreeHost(s->h_rec);
     if (s->h_err) cudaFreeHost(s->h_err);

@@ -37,8 +37,14 @@ SYMBOLS = (
     "lisa_sampler_get_counts", "lisa_sampler_step_launches", "lisa_sampler_destroy",
     "lisa_sampler_last_error", "lisa_sampler_to_physical", "lisa_sampler_from_physical",
     "lisa_sampler_sky_mode_init",
-    "lisa_autocorr_time",
+    "lisa_autocorr_time", "lisa_flow_default_schedule", "lisa_sampler_enable_flow",
+    "lisa_sampler_get_flow", "lisa_sampler_flow_stats",
+    # include/lisa_flow.h
+    "lisa_flow_create", "lisa_flow_destroy", "lisa_flow_last_error", "lisa_flow_set_weights",
+    "lisa_flow_get_weights", "lisa_flow_set_standardisation", "lisa_flow_get_standardisation",
+    "lisa_flow_normalize", "lisa_flow_generate", "lisa_flow_gradients", "lisa_flow_train",
 )
+FLOW_COUPLINGS, FLOW_HIDDEN, FLOW_PARAMS_PER_COUPLING = 8, 128, 20886
 LISA_TARGET_LIKELIHOOD, LISA_TARGET_GAUSSIAN = 0, 1
 SAMPLER_NDIM = 11
 NOALLOC_SCRATCH_BYTES = 4194304
@@ -79,6 +85,18 @@ class lisa_sampler_config(C.Structure):
         ("gauss_sigma", C.c_double * 11),
         ("use_graphs", C.c_int),
         ("timeout_s", C.c_double),
+    ]
+
+
+class lisa_flow_schedule(C.Structure):
+    _fields_ = [
+        ("train_every", C.c_int),
+        ("train_iters", C.c_int),
+        ("batch", C.c_int),
+        ("lr", C.c_double),
+        ("freeze_after", C.c_int),
+        ("seed", C.c_uint64),
+        ("flow_only", C.c_int),
     ]
 
 
@@ -166,6 +184,31 @@ def load(path: str = LIB_PATH):
     L.lisa_sampler_from_physical.argtypes = [vp, i, i, d, vp]
     L.lisa_sampler_sky_mode_init.argtypes = [vp, vp, vp, vp, i, i, u64, vp]
     L.lisa_autocorr_time.argtypes = [vp, i, i, i, i, dp, vp, vp]
+    fsp = C.POINTER(lisa_flow_schedule)
+    L.lisa_flow_default_schedule.argtypes = [fsp]
+    L.lisa_flow_default_schedule.restype = None
+    L.lisa_sampler_enable_flow.argtypes = [vp, fsp]
+    L.lisa_sampler_get_flow.argtypes = [vp]
+    L.lisa_sampler_get_flow.restype = vp
+    L.lisa_sampler_flow_stats.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
+    L.lisa_flow_create.argtypes = [u64, C.POINTER(vp)]
+    L.lisa_flow_destroy.argtypes = [vp]
+    L.lisa_flow_destroy.restype = None
+    L.lisa_flow_last_error.argtypes = [vp]
+    L.lisa_flow_last_error.restype = C.c_char_p
+    L.lisa_flow_set_weights.argtypes = [vp, vp]
+    L.lisa_flow_get_weights.argtypes = [vp, vp]
+    L.lisa_flow_set_standardisation.argtypes = [vp, vp, vp]
+    L.lisa_flow_get_standardisation.argtypes = [vp, vp, vp]
+    L.lisa_flow_normalize.argtypes = [vp, vp, i, vp, vp, vp]
+    L.lisa_flow_generate.argtypes = [vp, vp, i, vp, vp, vp]
+    L.lisa_flow_gradients.argtypes = [vp, vp, i, vp, dp, vp]
+    L.lisa_flow_train.argtypes = [vp, vp, i64, i, i, d, u64, u32, vp, vp]
+    for fn in ("lisa_sampler_enable_flow", "lisa_sampler_flow_stats", "lisa_flow_create",
+               "lisa_flow_set_weights", "lisa_flow_get_weights", "lisa_flow_set_standardisation",
+               "lisa_flow_get_standardisation", "lisa_flow_normalize", "lisa_flow_generate",
+               "lisa_flow_gradients", "lisa_flow_train"):
+        getattr(L, fn).restype = i
     for fn in ("lisa_sampler_create", "lisa_sampler_set_ladder", "lisa_sampler_set_state",
                "lisa_sampler_run", "lisa_sampler_get_state", "lisa_sampler_get_counts",
                "lisa_sampler_step_launches", "lisa_sampler_to_physical",
@@ -570,6 +613,23 @@ class LisaSampler:
     def step_launches(self):
         return lisa_sampler_step_launches(self.h)
 
+    def enable_flow(self, **kw):
+        """Flow proposals for the coldest temperature (lisa_flow_schedule fields as
+        keywords); returns the sampler's Flow (borrowed)."""
+        fs = lisa_flow_default_schedule()
+        for k, v in kw.items():
+            setattr(fs, k, v)
+        _scheck(load().lisa_sampler_enable_flow(self.h, C.byref(fs)), self.h)
+        self.flow = Flow(handle=load().lisa_sampler_get_flow(self.h))
+        return self.flow
+
+    def flow_stats(self):
+        acc = np.zeros(2, dtype=np.int64)
+        n = C.c_int()
+        loss = C.c_double()
+        _scheck(load().lisa_sampler_flow_stats(self.h, _ptr(acc), C.byref(n), C.byref(loss)), self.h)
+        return acc, n.value, loss.value
+
     def checkpoint(self, path):
         """Save what a resumed run needs (walkers, ladder, next step counter, seed) to an
         .npz file; ln L is re-evaluated on restore."""
@@ -604,3 +664,133 @@ def autocorr_time(chain, stride=1, offset=0, return_rho=False):
     torch.cuda.synchronize()
     tau = lisa_autocorr_time(t, n, W, stride, offset, rho)
     return (tau, rho) if return_rho else tau
+
+
+# ------------------------------------------------------------------- flow (lisa_flow.h)
+
+def lisa_flow_default_schedule() -> lisa_flow_schedule:
+    fs = lisa_flow_schedule()
+    load().lisa_flow_default_schedule(C.byref(fs))
+    return fs
+
+
+def _fcheck(st, f=None):
+    if st != LISA_OK:
+        msg = load().lisa_flow_last_error(f)
+        raise LisaError(st, msg.decode() if msg else "")
+
+
+def pack_flow_weights(w) -> np.ndarray:
+    """Dict of arrays (W1 [8,128,11], b1 [8,128], W2 [8,128,128], b2 [8,128],
+    W3 [8,22,128], b3 [8,22]) -> the packed [8][20886] float32 layout of lisa_flow.h."""
+    parts = [np.asarray(w[k], dtype=np.float32).reshape(FLOW_COUPLINGS, -1)
+             for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    out = np.ascontiguousarray(np.concatenate(parts, axis=1))
+    assert out.shape == (FLOW_COUPLINGS, FLOW_PARAMS_PER_COUPLING)
+    return out
+
+
+def unpack_flow_weights(p) -> dict:
+    p = np.asarray(p, dtype=np.float32).reshape(FLOW_COUPLINGS, FLOW_PARAMS_PER_COUPLING)
+    H, D = FLOW_HIDDEN, SAMPLER_NDIM
+    shapes = (("W1", (H, D)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (2 * D, H)),
+              ("b3", (2 * D,)))
+    out, o = {}, 0
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        out[k] = p[:, o:o + n].reshape((FLOW_COUPLINGS,) + shp).copy()
+        o += n
+    return out
+
+
+class Flow:
+    """One flow handle (owned, or borrowed from a sampler).  Device arrays are torch
+    tensors of float64 rows of 11 values."""
+
+    def __init__(self, seed=1, handle=None):
+        self.own = handle is None
+        if handle is None:
+            h = C.c_void_p()
+            _fcheck(load().lisa_flow_create(int(seed), C.byref(h)))
+            handle = h.value
+        self.h = C.c_void_p(handle)
+
+    def close(self):
+        if self.own and self.h is not None:
+            load().lisa_flow_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w):
+        p = pack_flow_weights(w) if isinstance(w, dict) else np.ascontiguousarray(w, np.float32)
+        _fcheck(load().lisa_flow_set_weights(self.h, _ptr(p)), self.h)
+
+    def weights(self):
+        p = np.empty((FLOW_COUPLINGS, FLOW_PARAMS_PER_COUPLING), np.float32)
+        _fcheck(load().lisa_flow_get_weights(self.h, _ptr(p)), self.h)
+        return unpack_flow_weights(p)
+
+    def set_standardisation(self, mu, sig):
+        m, s_ = _f64(mu), _f64(sig)
+        _fcheck(load().lisa_flow_set_standardisation(self.h, _ptr(m), _ptr(s_)), self.h)
+
+    def standardisation(self):
+        m, s_ = np.empty(SAMPLER_NDIM), np.empty(SAMPLER_NDIM)
+        _fcheck(load().lisa_flow_get_standardisation(self.h, _ptr(m), _ptr(s_)), self.h)
+        return m, s_
+
+    def _dev(self, a):
+        import torch
+
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+    def normalize(self, x):
+        import torch
+
+        dx = self._dev(x)
+        n = dx.shape[0]
+        z = torch.empty_like(dx)
+        lq = torch.empty(n, dtype=torch.float64, device=dx.device)
+        torch.cuda.synchronize()
+        _fcheck(load().lisa_flow_normalize(self.h, _ptr(dx), n, _ptr(z), _ptr(lq), None), self.h)
+        torch.cuda.synchronize()
+        return z.cpu().numpy(), lq.cpu().numpy()
+
+    def generate(self, z):
+        import torch
+
+        dz = self._dev(z)
+        n = dz.shape[0]
+        x = torch.empty_like(dz)
+        lq = torch.empty(n, dtype=torch.float64, device=dz.device)
+        torch.cuda.synchronize()
+        _fcheck(load().lisa_flow_generate(self.h, _ptr(dz), n, _ptr(x), _ptr(lq), None), self.h)
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), lq.cpu().numpy()
+
+    def gradients(self, x):
+        import torch
+
+        dx = self._dev(x)
+        g = np.empty((FLOW_COUPLINGS, FLOW_PARAMS_PER_COUPLING), np.float32)
+        loss = C.c_double()
+        torch.cuda.synchronize()
+        _fcheck(load().lisa_flow_gradients(self.h, _ptr(dx), dx.shape[0], _ptr(g),
+                                           C.byref(loss), None), self.h)
+        return loss.value, unpack_flow_weights(g)
+
+    def train(self, data, iters, batch=1024, lr=1e-3, seed=1, round_=0):
+        import torch
+
+        dd = data if hasattr(data, "data_ptr") else self._dev(data)
+        loss = np.empty(iters)
+        torch.cuda.synchronize()
+        _fcheck(load().lisa_flow_train(self.h, _ptr(dd), dd.shape[0], int(iters), int(batch),
+                                       float(lr), int(seed), int(round_), _ptr(loss), None),
+                self.h)
+        return loss
