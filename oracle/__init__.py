@@ -75,6 +75,7 @@ def lib():
             L.oracle_spline_eval.restype = None
             L.oracle_template.argtypes = [dp, d, ip, i, i, d, d, i64, dp]
             L.oracle_direct.argtypes = [dp, d, ip, i, d, d, i64, dp]
+            L.oracle_mode_response.argtypes = [dp, d, i, i, d, d, i64, dp, i64, dp]
             L.oracle_inner.argtypes = [dp, dp, dp, d, i64]
             L.oracle_inner.restype = d
             L.oracle_loglike.argtypes = [dp, i, d, ip, i, i, d, d, i64, dp, dp, i, dp, dp, dp, dp]
@@ -226,6 +227,17 @@ def direct(th, t0, modes, f0, df, n_bins):
     h = np.empty((3, n_bins, 2))
     lib().oracle_direct(_dp(_f64(th)), t0, md.ctypes.data_as(C.POINTER(C.c_int)), len(md), f0,
                         df, n_bins, _dp(h))
+    return h[..., 0] + 1j * h[..., 1]
+
+
+def mode_response(th, t0, l, m, f0, df, n_bins, f):
+    """One mode's A, E, T response [3, n] (complex) at arbitrary frequencies f (direct
+    evaluation; zero outside the mode's band on the grid)."""
+    f = _f64(f)
+    h = np.empty((3, f.size, 2))
+    if not lib().oracle_mode_response(_dp(_f64(th)), t0, l, m, f0, df, n_bins, _dp(f), f.size,
+                                      _dp(h)):
+        raise ValueError("invalid parameters or mode")
     return h[..., 0] + 1j * h[..., 1]
 
 

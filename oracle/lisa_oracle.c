@@ -728,6 +728,36 @@ int oracle_direct(const double *th, double t0, const int *modes, int n_modes, do
     return 1;
 }
 
+/* one mode's A, E, T response at arbitrary frequencies f[n] by direct evaluation, zero
+ * outside the mode's band [f_lo, f_hi] on the grid (f0, df, n_bins); h [3][n][2] */
+int oracle_mode_response(const double *th, double t0, int l, int m, double f0, double df,
+                         int64_t n_bins, const double *f, int64_t n, double *h)
+{
+    wf_t w;
+    memset(h, 0, sizeof(double) * 6 * (size_t)n);
+    if (!mode_ok(l, m) || !derive(th, t0, &w)) return 0;
+    double flo, fhi;
+    int64_t jl, jh;
+    if (!band_of(&w, l, m, f0, df, n_bins, &flo, &fhi, &jl, &jh)) return 1;
+    double complex Kp, Kc;
+    pol_factors(&w, l, m, &Kp, &Kc);
+    for (int64_t i = 0; i < n; i++) {
+        const double fi = f[i];
+        if (!(fi >= flo && fi <= fhi)) continue;
+        double t = mode_time(&w, l, m, fi);
+        double complex T[3];
+        transfer_at(&w, Kp, Kc, fi, t, T);
+        double ph = mode_phase(&w, l, m, fi) + delay_phase(&w, fi, t) - 2.0 * PI * fi * w.tc;
+        double complex z = mode_amp(&w, l, m, fi) * cexp(I * ph);
+        for (int c = 0; c < 3; c++) {
+            double complex hx = T[c] * z;
+            h[2 * (c * n + i)] = creal(hx);
+            h[2 * (c * n + i) + 1] = cimag(hx);
+        }
+    }
+    return 1;
+}
+
 /* ------------------------------------------------------------------------- */
 /* inner products and likelihood: Eqs. (2), (3), (11)                          */
 /* ------------------------------------------------------------------------- */

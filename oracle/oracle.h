@@ -81,6 +81,11 @@ int oracle_template(const double *th, double t0, const int *modes, int n_modes, 
 int oracle_direct(const double *th, double t0, const int *modes, int n_modes,
                   double f0, double df, int64_t n_bins, double *h);
 
+/* one mode's A, E, T response at arbitrary frequencies (direct evaluation), zero outside
+ * the mode's band on the grid; h [3][n][2] */
+int oracle_mode_response(const double *th, double t0, int l, int m, double f0, double df,
+                         int64_t n_bins, const double *f, int64_t n, double *h);
+
 /* noise-weighted inner products of Eqs. (3) and (11): re<a|b> summed over A,E,T */
 double oracle_inner(const double *a, const double *b, const double *psd, double df, int64_t n_bins);
 
