@@ -276,7 +276,8 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B,
                     device=torch.cuda.current_device(), precision=lisalike.LISA_PREC_SPLIT)
     make_inputs(lisalike, like, g, 1, 1)          # same data as the FP64 handle
-    lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    if not args.no_autotune:
+        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
     dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
     lnL = torch.empty(B, dtype=torch.float64, device="cuda")
 
@@ -352,9 +353,8 @@ def sampler_cpu_baseline(steps=4):
             "seconds": dt}
 
 
-def run_sampler(args, world, rank, local):
-    """The sampler workload: K timed steps after W warm-up (burn-in) steps; value =
-    sampler steps per second of the whole job (each step evaluates every walker once)."""
+def sampler_setup(args, rank, local):
+    """Likelihood with the sampler workload's data, starting walkers, tile shapes."""
     import torch
 
     from paper_2005_01827_gb300 import LisaLike, build, lisalike as LL
@@ -386,8 +386,59 @@ def run_sampler(args, world, rank, local):
     dth = torch.empty_like(dx)
     LL.lisa_sampler_to_physical(dx, dx.shape[0], True, W.T0_YEAR, dth, stream.cuda_stream)
     stream.synchronize()
-    th_start = dth.cpu().numpy()
-    LL.lisa_like_autotune(like.h, th_start[:256], 256)
+    LL.lisa_like_autotune(like.h, dth.cpu().numpy()[:256], 256)
+    return LL, like, stream, x0, prec
+
+
+def like_roofline(LL, like, xs, prec, stream):
+    """One profiled likelihood call on a sampler-sized batch (half of the walkers of every
+    temperature, converted to physical parameters): stage times and the dense kernel's
+    roofline."""
+    import torch
+
+    T, Wk = W.SAMPLER_T, W.SAMPLER_W
+    B = T * Wk // 2
+    dx = torch.tensor(xs.reshape(-1, 11)[:B], dtype=torch.float64, device="cuda")
+    dth = torch.empty_like(dx)
+    LL.lisa_sampler_to_physical(dx, B, True, W.T0_YEAR, dth, stream.cuda_stream)
+    stream.synchronize()
+    lnl_b = torch.empty(B, dtype=torch.float64, device="cuda")
+
+    def like_call():
+        LL.lisa_like_loglike_device(like.h, dth, B, lnl_b, None, None, stream.cuda_stream)
+
+    like_call()
+    stage_ms, ncalls = profile_once(LL, like, like_call)
+    mode_bins, bins = work_units(like, dth.cpu().numpy())
+    dense_ms = stage_ms[4] / max(ncalls, 1)
+    flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
+    achieved = flops / (dense_ms * 1e-3) / 1e12
+    split = prec == LL.LISA_PREC_SPLIT
+    peak = fp32_peak_tflops() if split else fp64_peak_tflops()
+    roof = {"bound": "alu", "kernel": "dense_split_kernel" if split else "dense_f64_kernel",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "note": "one profiled likelihood call on the sampler's batch of %d walkers after "
+                    "the timed steps" % B,
+            "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
+                                  zip(("knots", "splines", "segprep", "plan", "dense",
+                                       "finish"), stage_ms)}}
+    return roof, sum(stage_ms) / max(ncalls, 1)
+
+
+def chain_stats(LL, chain, K, Wk, stream):
+    taus = [LL.lisa_autocorr_time(chain, K, Wk, 11, q, None, stream.cuda_stream)
+            for q in range(11)]
+    return taus, float(np.nanmax(taus))
+
+
+def run_sampler(args, world, rank, local):
+    """The sampler workload: K timed steps after W warm-up (burn-in) steps; value =
+    sampler steps per second of the whole job (each step evaluates every walker once)."""
+    import torch
+
+    LL, like, stream, x0, prec = sampler_setup(args, rank, local)
+    T, Wk = W.SAMPLER_T, W.SAMPLER_W
     s = LL.LisaSampler(like, seed=11 + rank)
     s.set_state(x0)
     s.run(max(args.warmup, 3), record=False)          # burn-in; also captures the graph
@@ -410,32 +461,11 @@ def run_sampler(args, world, rank, local):
     acc1, sw1 = s.counts()
     launches = K * s.step_launches()
     xs, lnls, betas, step = s.state()
-    taus = [LL.lisa_autocorr_time(chain, K, Wk, 11, q, None, stream.cuda_stream)
-            for q in range(11)]
-    tau = float(np.nanmax(taus))
+    taus, tau = chain_stats(LL, chain, K, Wk, stream)
     sec = ms * 1e-3
     value = world * K / sec
     ess = K * Wk / tau
-    # the likelihood inside a step: one profiled call on the current proposals' batch
-    # size, with the current walkers of every temperature (half of them)
-    dx = torch.tensor(xs.reshape(-1, 11)[: T * Wk // 2], dtype=torch.float64, device="cuda")
-    LL.lisa_sampler_to_physical(dx, dx.shape[0], True, W.T0_YEAR, dth, stream.cuda_stream)
-    stream.synchronize()
-    thn = dth.cpu().numpy()
-    lnl_b = torch.empty(T * Wk // 2, dtype=torch.float64, device="cuda")
-
-    def like_call():
-        LL.lisa_like_loglike_device(like.h, dth, T * Wk // 2, lnl_b, None, None,
-                                    stream.cuda_stream)
-
-    like_call()
-    stage_ms, ncalls = profile_once(LL, like, like_call)
-    mode_bins, bins = work_units(like, thn)
-    dense_ms = stage_ms[4] / max(ncalls, 1)
-    flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
-    achieved = flops / (dense_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops() if prec == LL.LISA_PREC_SPLIT else fp64_peak_tflops()
-    like_ms = sum(stage_ms) / max(ncalls, 1)
+    roofline, like_ms = like_roofline(LL, like, xs, prec, stream)
     # sampler kernels alone: the same ensemble on the Gaussian target
     gs = LL.LisaSampler(None, n_temps=T, n_walkers=Wk, target=LL.LISA_TARGET_GAUSSIAN,
                         lisa_frame=1, seed=3)
@@ -473,17 +503,100 @@ def run_sampler(args, world, rank, local):
                      "note": "tau from a chain shorter than 50 tau is a lower bound"},
             "step_breakdown_ms": {"likelihood_per_call": like_ms, "likelihood_calls": 2,
                                   "sampler_kernels_per_step": own_ms},
-            "roofline": {"bound": "alu", "kernel": "dense_split_kernel" if prec == LL.LISA_PREC_SPLIT
-                         else "dense_f64_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "note": "one profiled likelihood call on the sampler's batch of %d "
-                                 "walkers after the timed steps" % (T * Wk // 2),
-                         "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
-                                               zip(("knots", "splines", "segprep", "plan",
-                                                    "dense", "finish"), stage_ms)}},
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = sampler_cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+FLOW_METRIC = ("MCMC ESS/s of the coldest chain, flow proposal (8 couplings, bf16) vs plain "
+               "stretch moves (8 temps x 256 walkers, 6 modes, A/E/T, 1-yr df)")
+
+
+def run_flow(args, world, rank, local):
+    """Config-5 comparison: the same sampler, start and burn-in with and without flow
+    proposals (trained on the coldest chain every 500 steps until the end of burn-in);
+    value = effective samples per second of the coldest chain with the flow."""
+    import torch
+
+    LL, like, stream, x0, prec = sampler_setup(args, rank, local)
+    T, Wk = W.SAMPLER_T, W.SAMPLER_W
+    every = args.train_every
+    burn = max(args.warmup, 2 * every)
+    K = args.steps
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for use_flow in (False, True):
+        s = LL.LisaSampler(like, seed=11 + rank)
+        if use_flow:
+            s.enable_flow(train_every=every, train_iters=400, batch=1024, lr=1e-3, seed=3,
+                          freeze_after=burn)
+        s.set_state(x0)
+        t0 = time.perf_counter()
+        s.run(burn, record=False)
+        burn_s = time.perf_counter() - t0
+        chain = torch.empty((K, Wk, 11), dtype=torch.float64, device="cuda")
+        lch = torch.empty((K, Wk), dtype=torch.float64, device="cuda")
+        acc0, _ = s.counts()
+        f0 = s.flow_stats()[0] if use_flow else None
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.run_device(K, chain, lch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(world, e0.elapsed_time(e1))
+        acc1, _ = s.counts()
+        taus, tau = chain_stats(LL, chain, K, Wk, stream)
+        c = chain.cpu().numpy().reshape(-1, 11)
+        r = {"ms_per_step": ms / K, "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
+             "ess": K * Wk / tau, "ess_per_s": world * K * Wk / tau / (ms * 1e-3),
+             "stretch_acceptance_cold": float((acc1 - acc0)[0, 0] / max((acc1 - acc0)[0, 1], 1)),
+             "burn_in_s": burn_s, "launches_per_step": s.step_launches(),
+             "mean": c.mean(axis=0).tolist(), "std": c.std(axis=0).tolist()}
+        if use_flow:
+            f1, n_tr, loss = s.flow_stats()
+            r["flow_acceptance"] = float((f1 - f0)[0] / max((f1 - f0)[1], 1))
+            r["trainings"] = n_tr
+            r["last_training_loss"] = loss
+        out["flow" if use_flow else "plain"] = r
+        xs, _, _, _ = s.state()
+        s.close()
+    clk = clocks.stop()
+    roofline, like_ms = like_roofline(LL, like, xs, prec, stream)
+    like.close()
+    p, f = out["plain"], out["flow"]
+    sd = np.array(p["std"])
+    accuracy = {"max_abs_mean_diff_over_std": float(np.max(np.abs(np.array(f["mean"]) -
+                                                                   np.array(p["mean"])) / sd)),
+                "std_ratio_range": [float(np.min(np.array(f["std"]) / sd)),
+                                    float(np.max(np.array(f["std"]) / sd))]}
+    line = {"metric": FLOW_METRIC, "value": f["ess_per_s"], "unit": "effective samples/s",
+            "n_gpus": world, "steps": K, "warmup": burn, "ms_per_step": f["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == LL.LISA_PREC_SPLIT else "f64", "data": "synthetic",
+            "config": {"workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
+                       "(11-128-128-22, bf16 mma.sync, FP32 accumulate), trained every 500 "
+                       "steps on the coldest chain until the end of burn-in, independence MH "
+                       "on the coldest temperature every step",
+                       "precision": args.precision, "graphs": True,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (data 227 MB, spline coefficients 0.8 GB)"},
+            "flow_over_plain_ess_per_s": f["ess_per_s"] / p["ess_per_s"],
+            "plain": p, "flow": f, "posterior_agreement": accuracy,
+            "roofline": roofline, "gpu_launches": K * (p["launches_per_step"] + f["launches_per_step"]),
+            "clocks": clk,
+            "e2e": {"value": f["ess_per_s"], "unit": "effective samples/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "device-resident chains; the host reads them once after the run"}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -515,18 +628,27 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true",
                     help="skip the split-precision timing of the same workload")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "sampler"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "sampler", "flow"],
                     help="c2: the 1024-walker benchmark workload; c3: 8192 walkers with "
                          "masses 1e3..1e9 Msun under CUDA-graph replay with autotuned tiles; "
-                         "sampler: the parallel-tempered ensemble sampler on the likelihood")
+                         "sampler: the parallel-tempered ensemble sampler on the likelihood; "
+                         "flow: ESS/s of the sampler with and without flow proposals")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"],
                     help="likelihood precision of the sampler workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shape (8 bins per thread, groups of 8); for "
+                         "profiling captures that must see one known kernel variant")
+    ap.add_argument("--train-every", type=int, default=500,
+                    help="flow workload: steps between flow trainings (500 is the workload; "
+                         "smaller only for profiling captures)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, world, rank)
     if args.workload == "sampler":
         return run_sampler(args, world, rank, local)
+    if args.workload == "flow":
+        return run_flow(args, world, rank, local)
 
     import torch
 
@@ -542,7 +664,8 @@ def main():
                      (3.0, 9.0) if c3 else (5.0, 7.0))
     mode_bins, bins = work_units(like, th)
     # tile shapes from the autotuner (timed on a 256-walker sample of the workload)
-    lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    if not args.no_autotune:
+        lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
 
     # a dedicated stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()

@@ -5,14 +5,16 @@ The flow is not part of the paper: it is an independence proposal for the
 Metropolis-Hastings rule of Eq. (13), whose acceptance min(1, L(y)/L(x) Q(x)/Q(y))
 keeps the chain exact for any proposal density Q.  Definitions written out here:
 
-* Standardisation u = (x - mu) / sigma per coordinate (mu, sigma of the training set).
+* Whitening u = L^{-1} (x - mu), mu the mean and L L^T the covariance of the training
+  set (Cholesky factor, each pivot floored at 1e-12 of its diagonal entry); a vector
+  sigma stands for L = diag(sigma).
 * Eight affine coupling layers.  Layer c keeps the coordinates with mask m_c = 1 and
   maps the others: v = m u + (1 - m) (u - t) e^{-s}, with s = (1 - m) S tanh(o_s / S),
   t = (1 - m) o_t, S = 2, and (o_s, o_t) = W3 relu(W2 relu(W1 (m u) + b1) + b2) + b3
   (11 -> 128 -> 128 -> 22).  log |dv/du| = -sum s.  Masks: c mod 4 = 0 keeps the even
   coordinates, 1 the odd ones, 2 coordinates 0..5, 3 coordinates 6..10.
 * Density: z = layers(u), log q(x) = -|z|^2/2 - (D/2) log 2 pi + sum_c log|det_c|
-  - sum_d log sigma_d.  Sampling runs the layers backwards from z ~ N(0, I):
+  - sum_d log L_dd.  Sampling runs the layers backwards from z ~ N(0, I):
   u = m v + (1 - m) (v e^{s} + t), s and t from m v (= m u).
 * BF16 arithmetic of the networks: every GEMM operand (weights, layer inputs, hidden
   activations and, in training, the back-propagated gradients) is rounded to bfloat16
@@ -68,17 +70,33 @@ def mlp(w, c, u, m, quant=True):
     return s, t, (a0, z1, a1, z2, a2, th)
 
 
+def as_factor(sig):
+    """The whitening factor L (lower triangular) from a factor or a vector of scales."""
+    sig = np.asarray(sig, dtype=np.float64)
+    return np.diag(sig) if sig.ndim == 1 else sig
+
+
+def whiten(x, mu, sig):
+    """u = L^{-1} (x - mu) by forward substitution, rows of x."""
+    L = as_factor(sig)
+    y = np.asarray(x, dtype=np.float64) - mu
+    u = np.zeros_like(y)
+    for d in range(D):
+        u[:, d] = (y[:, d] - u[:, :d] @ L[d, :d]) / L[d, d]
+    return u
+
+
 def normalize(w, x, mu, sig, quant=True):
     """x [n, D] -> z [n, D] and log q(x) [n]."""
     m = masks()
-    u = (np.asarray(x, dtype=np.float64) - mu) / sig
+    u = whiten(x, mu, sig)
     logdet = np.zeros(u.shape[0])
     for c in range(C):
         s, t, _ = mlp(w, c, u, m[c], quant)
         u = m[c] * u + (1.0 - m[c]) * (u - t) * np.exp(-s)
         logdet -= s.sum(axis=1)
     logq = -0.5 * np.sum(u * u, axis=1) - 0.5 * D * math.log(2 * math.pi) + logdet
-    return u, logq - np.sum(np.log(sig))
+    return u, logq - np.sum(np.log(np.diag(as_factor(sig))))
 
 
 def generate(w, z, mu, sig, quant=True):
@@ -90,7 +108,8 @@ def generate(w, z, mu, sig, quant=True):
         s, t, _ = mlp(w, c, v, m[c], quant)
         v = m[c] * v + (1.0 - m[c]) * (v * np.exp(s) + t)
         logq -= s.sum(axis=1)
-    return mu + sig * v, logq - np.sum(np.log(sig))
+    L = as_factor(sig)
+    return mu + v @ L.T, logq - np.sum(np.log(np.diag(L)))
 
 
 def nll_grads(w, u, quant=True):
@@ -154,22 +173,34 @@ def adam_state(w):
             {k: np.zeros(v.shape) for k, v in w.items()})
 
 
-def standardisation(x):
+def whitening(x):
+    """Mean and Cholesky factor of the (population) covariance of the rows of x."""
     x = np.asarray(x, dtype=np.float64)
-    return x.mean(axis=0), np.maximum(x.std(axis=0), 1e-12)
+    mu = x.mean(axis=0)
+    C = (x - mu).T @ (x - mu) / x.shape[0]
+    L = np.zeros((D, D))
+    for i in range(D):
+        for j in range(i + 1):
+            acc = C[i, j] - L[i, :j] @ L[j, :j]
+            if i == j:
+                floor = 1e-12 * C[i, i] if C[i, i] > 0 else 1e-300
+                L[i, i] = math.sqrt(max(acc, floor))
+            else:
+                L[i, j] = acc / L[j, j]
+    return mu, L
 
 
 def train(w, data, n_iter, batch, lr, index_fn, quant=True):
-    """Adam on minibatches data[index_fn(i)]; returns weights, standardisation, losses."""
-    mu, sig = standardisation(data)
-    u = (data - mu) / sig
+    """Adam on minibatches data[index_fn(i)]; returns weights, whitening, losses."""
+    mu, L = whitening(data)
+    u = whiten(data, mu, L)
     st = adam_state(w)
     losses = []
     for i in range(n_iter):
         loss, g = nll_grads(w, u[index_fn(i, batch, data.shape[0])], quant)
         w, st = adam(w, g, st, lr)
         losses.append(loss)
-    return w, mu, sig, np.array(losses)
+    return w, mu, L, np.array(losses)
 
 
 # ----------------------------------------------------------------- proposal and MH step

@@ -266,8 +266,25 @@ __device__ float couple_row(SmemNet &sm, int c, int row, bool gen) {
 struct FlowView {
     const float *w;
     const bf16 *wb;
-    const double *mu, *sig;
+    const double *mu, *L;  // mean [11], lower-triangular whitening factor [11][11]
 };
+
+// u = L^{-1} (x - mu) by forward substitution (FP64), written as FP32
+__device__ inline void whiten_row(const double *x, const double *mu, const double *L, float *u) {
+    double v[FD];
+    for (int d = 0; d < FD; d++) {
+        double acc = x[d] - mu[d];
+        for (int j = 0; j < d; j++) acc -= L[d * FD + j] * v[j];
+        v[d] = acc / L[d * FD + d];
+        u[d] = (float)v[d];
+    }
+}
+
+__device__ inline double log_det_factor(const double *L) {
+    double s = 0.0;
+    for (int d = 0; d < FD; d++) s += log(L[d * FD + d]);
+    return s;
+}
 
 // Both directions for up to 64 rows per block.  Normalizing: in = x, out = z;
 // generating: in = z, out = x.  logq = log q(x) in both cases.
@@ -278,14 +295,16 @@ __global__ void __launch_bounds__(NTH) flow_eval_kernel(FlowView f, const double
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r0 = warp * 16;
     const int row0 = blockIdx.x * TS;
     double lq = 0.0;  // lanes 0..15: the row r0 + lane
-    for (int i = threadIdx.x; i < TS * LU; i += NTH) {
-        const int r = i / LU, d = i % LU;
-        float v = 0.0f;
-        if (d < FD && row0 + r < n) {
-            const double xv = in[(size_t)(row0 + r) * FD + d];
-            v = gen ? (float)xv : (float)((xv - f.mu[d]) / f.sig[d]);
+    if (threadIdx.x < TS) {
+        const int r = threadIdx.x, row = row0 + r;
+        float *u = sm.u + r * LU;
+        for (int d = 0; d < LU; d++) u[d] = 0.0f;
+        if (row < n) {
+            if (gen)
+                for (int d = 0; d < FD; d++) u[d] = (float)in[(size_t)row * FD + d];
+            else
+                whiten_row(in + (size_t)row * FD, f.mu, f.L, u);
         }
-        sm.u[i] = v;
     }
     __syncthreads();
     if (gen && lane < 16) {
@@ -311,12 +330,14 @@ __global__ void __launch_bounds__(NTH) flow_eval_kernel(FlowView f, const double
     if (lane < 16) {
         const int rr = r0 + lane, row = row0 + rr;
         if (row < n) {
-            double zz = 0.0, lsig = 0.0;
+            const double lsig = log_det_factor(f.L);
+            double zz = 0.0;
             for (int d = 0; d < FD; d++) {
                 const double v = sm.u[rr * LU + d];
-                lsig += log(f.sig[d]);
                 if (gen) {
-                    out[(size_t)row * FD + d] = f.mu[d] + f.sig[d] * v;
+                    double xv = f.mu[d];  // x = mu + L v
+                    for (int j = 0; j <= d; j++) xv += f.L[d * FD + j] * (double)sm.u[rr * LU + j];
+                    out[(size_t)row * FD + d] = xv;
                 } else {
                     zz += v * v;
                     if (out) out[(size_t)row * FD + d] = v;
@@ -332,7 +353,7 @@ struct TrainArgs {
     const float *w;
     const bf16 *wb;
     float *grad;            // [8][PC], accumulated
-    const double *mu, *sig;
+    const double *mu, *L;
     const double *data;     // [n][11]
     long long n;
     int batch;              // rows of this minibatch (multiple of 64)
@@ -348,21 +369,17 @@ __global__ void __launch_bounds__(NTH) flow_train_kernel(TrainArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r0 = warp * 16;
     const int g = lane >> 2, t = lane & 3;
     const float inv_n = 1.0f / (float)a.batch;
-    // minibatch rows, standardised
-    for (int i = threadIdx.x; i < TS * LU; i += NTH) {
-        const int r = i / LU, d = i % LU;
-        float v = 0.0f;
-        if (d < FD) {
-            const int j = blockIdx.x * TS + r;
-            long long idx = j;
-            if (a.random_rows) {
-                const lisa_smp::U4 q = lisa_smp::philox(a.round, 5u, a.iter, (uint32_t)(j >> 2), a.k0, a.k1);
-                idx = (long long)(lisa_smp::unit(q.v[j & 3]) * (double)a.n);
-                if (idx > a.n - 1) idx = a.n - 1;
-            }
-            v = (float)((a.data[idx * FD + d] - a.mu[d]) / a.sig[d]);
+    // minibatch rows, whitened
+    if (threadIdx.x < TS) {
+        const int r = threadIdx.x, j = blockIdx.x * TS + r;
+        long long idx = j;
+        if (a.random_rows) {
+            const lisa_smp::U4 q = lisa_smp::philox(a.round, 5u, a.iter, (uint32_t)(j >> 2), a.k0, a.k1);
+            idx = (long long)(lisa_smp::unit(q.v[j & 3]) * (double)a.n);
+            if (idx > a.n - 1) idx = a.n - 1;
         }
-        sm.u[i] = v;
+        sm.u[r * LU + FD] = 0.0f;
+        whiten_row(a.data + idx * FD, a.mu, a.L, sm.u + r * LU);
     }
     __syncthreads();
     float ssum = 0.0f;  // lanes 0..15: the row's sum of s
@@ -566,8 +583,8 @@ __global__ void pack_kernel(const float *w, bf16 *wb) {
     wb[i] = __float2bfloat16_rn(v);
 }
 
-// mean and standard deviation of each coordinate (one block per coordinate, FP64)
-__global__ void standardise_kernel(const double *x, long long n, double *mu, double *sig) {
+// mean of each coordinate (one block per coordinate, FP64)
+__global__ void mean_kernel(const double *x, long long n, double *mu) {
     __shared__ double red[256];
     const int d = blockIdx.x;
     double s = 0.0;
@@ -578,23 +595,49 @@ __global__ void standardise_kernel(const double *x, long long n, double *mu, dou
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    const double mean = red[0] / (double)n;
-    __syncthreads();
-    double q = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const double e = x[i * FD + d] - mean;
-        q += e * e;
+    if (threadIdx.x == 0) mu[d] = red[0] / (double)n;
+}
+
+// covariance entry (i, j), i >= j, one block each (population normalisation)
+__global__ void cov_kernel(const double *x, long long n, const double *mu, double *cov) {
+    __shared__ double red[256];
+    int b = blockIdx.x, i = 0;
+    while (b > i) {
+        b -= i + 1;
+        i++;
     }
-    red[threadIdx.x] = q;
+    const int j = b;
+    double s = 0.0;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x)
+        s += (x[r * FD + i] - mu[i]) * (x[r * FD + j] - mu[j]);
+    red[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        mu[d] = mean;
-        sig[d] = fmax(sqrt(red[0] / (double)n), 1e-12);
+        cov[i * FD + j] = red[0] / (double)n;
+        cov[j * FD + i] = red[0] / (double)n;
     }
+}
+
+// Cholesky factor of the covariance, each pivot floored at 1e-12 of its diagonal entry
+__global__ void cholesky_kernel(const double *cov, double *L) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < FD * FD; i++) L[i] = 0.0;
+    for (int i = 0; i < FD; i++)
+        for (int j = 0; j <= i; j++) {
+            double acc = cov[i * FD + j];
+            for (int k = 0; k < j; k++) acc -= L[i * FD + k] * L[j * FD + k];
+            if (i == j) {
+                const double cii = cov[i * FD + i];
+                const double floor = cii > 0.0 ? 1e-12 * cii : 1e-300;
+                L[i * FD + i] = sqrt(fmax(acc, floor));
+            } else {
+                L[i * FD + j] = acc / L[j * FD + j];
+            }
+        }
 }
 
 // ------------------------------------------------------------------ sampler step
@@ -646,20 +689,25 @@ __global__ void __launch_bounds__(NTH) flow_propose_kernel(FlowView f, lisa_flow
         __syncwarp();
         __syncthreads();
     }
-    double lsig = 0.0;
-    for (int d = 0; d < FD; d++) lsig += log(f.sig[d]);
+    const double lsig = log_det_factor(f.L);
     if (lane < 16) {
         const int rr = r0 + lane, w = w0 + rr;
         if (w < a.W) {
-            for (int d = 0; d < FD; d++) a.fy[(size_t)w * FD + d] = f.mu[d] + f.sig[d] * (double)sm.u[rr * LU + d];
+            for (int d = 0; d < FD; d++) {
+                double xv = f.mu[d];  // y = mu + L v
+                for (int j = 0; j <= d; j++) xv += f.L[d * FD + j] * (double)sm.u[rr * LU + j];
+                a.fy[(size_t)w * FD + d] = xv;
+            }
             qy[rr] += lq - lsig;
         }
     }
     __syncthreads();
     // log q of the current walkers
-    for (int i = threadIdx.x; i < TS * LU; i += NTH) {
-        const int r = i / LU, d = i % LU, w = w0 + r;
-        sm.u[i] = (d < FD && w < a.W) ? (float)((a.x[(size_t)w * FD + d] - f.mu[d]) / f.sig[d]) : 0.0f;
+    if (threadIdx.x < TS) {
+        const int r = threadIdx.x, w = w0 + r;
+        float *u = sm.u + r * LU;
+        for (int d = 0; d < LU; d++) u[d] = 0.0f;
+        if (w < a.W) whiten_row(a.x + (size_t)w * FD, f.mu, f.L, u);
     }
     __syncthreads();
     lq = 0.0;
@@ -728,7 +776,7 @@ struct lisa_flow {
     int device = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     bf16 *wb = nullptr;
-    double *mu = nullptr, *sig = nullptr, *loss = nullptr;
+    double *mu = nullptr, *L = nullptr, *cov = nullptr, *loss = nullptr;
     int loss_cap = 0, last_iters = 0;
     float *h_grad = nullptr;
     std::string err;
@@ -753,7 +801,7 @@ lisa_status fcuda(lisa_flow_t *f, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return fcuda(f, e_, what); \
     } while (0)
 
-FlowView view(const lisa_flow_t *f) { return {f->w, f->wb, f->mu, f->sig}; }
+FlowView view(const lisa_flow_t *f) { return {f->w, f->wb, f->mu, f->L}; }
 
 cudaError_t set_smem_limits() {
     cudaError_t e = cudaFuncSetAttribute(flow_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, eval_smem());
@@ -791,7 +839,7 @@ lisa_status train_iters(lisa_flow_t *f, const double *d_data, int64_t n, int ite
         a.wb = f->wb;
         a.grad = f->g;
         a.mu = f->mu;
-        a.sig = f->sig;
+        a.L = f->L;
         a.data = d_data;
         a.n = n;
         a.batch = batch;
@@ -833,8 +881,10 @@ cudaError_t launch_flow_accept(const FStep &a, cudaStream_t s) {
 
 lisa_status flow_train_async(lisa_flow_t *f, const double *d_data, int64_t n, int iters,
                              int batch, double lr, uint64_t seed, uint32_t round, cudaStream_t s) {
-    standardise_kernel<<<FD, 256, 0, s>>>(d_data, n, f->mu, f->sig);
-    FCK(cudaGetLastError(), "standardisation kernel launch");
+    mean_kernel<<<FD, 256, 0, s>>>(d_data, n, f->mu);
+    cov_kernel<<<FD * (FD + 1) / 2, 256, 0, s>>>(d_data, n, f->mu, f->cov);
+    cholesky_kernel<<<1, 32, 0, s>>>(f->cov, f->L);
+    FCK(cudaGetLastError(), "whitening kernel launch");
     FCK(cudaMemsetAsync(f->m, 0, sizeof(float) * NP, s), "cudaMemsetAsync");
     FCK(cudaMemsetAsync(f->v, 0, sizeof(float) * NP, s), "cudaMemsetAsync");
     return train_iters(f, d_data, n, iters, batch, lr, seed, round, s, 1);
@@ -870,7 +920,8 @@ lisa_status lisa_flow_create(uint64_t seed, lisa_flow_t **out) {
         if (e == cudaSuccess) e = cudaMalloc(&f->v, sizeof(float) * NP);
         if (e == cudaSuccess) e = cudaMalloc(&f->wb, sizeof(bf16) * FC * BC);
         if (e == cudaSuccess) e = cudaMalloc(&f->mu, sizeof(double) * FD);
-        if (e == cudaSuccess) e = cudaMalloc(&f->sig, sizeof(double) * FD);
+        if (e == cudaSuccess) e = cudaMalloc(&f->L, sizeof(double) * FD * FD);
+        if (e == cudaSuccess) e = cudaMalloc(&f->cov, sizeof(double) * FD * FD);
         if (e == cudaSuccess) e = cudaMallocHost(&f->h_grad, sizeof(float) * NP);
         if (e != cudaSuccess) {
             st = fcuda(f, e, "flow allocation");
@@ -893,8 +944,9 @@ lisa_status lisa_flow_create(uint64_t seed, lisa_flow_t **out) {
         }
         st = lisa_flow_set_weights(f, w.data());
         if (st != LISA_OK) break;
-        std::vector<double> mu(FD, 0.0), sg(FD, 1.0);
-        st = lisa_flow_set_standardisation(f, mu.data(), sg.data());
+        std::vector<double> mu(FD, 0.0), L(FD * FD, 0.0);
+        for (int d = 0; d < FD; d++) L[d * FD + d] = 1.0;
+        st = lisa_flow_set_whitening(f, mu.data(), L.data());
     } while (0);
     if (st != LISA_OK) {
         lisa::set_thread_error(f->err);
@@ -910,7 +962,7 @@ void lisa_flow_destroy(lisa_flow_t *f) {
     cudaSetDevice(f->device);
     cudaDeviceSynchronize();
     for (void *p : {(void *)f->w, (void *)f->g, (void *)f->m, (void *)f->v, (void *)f->wb,
-                    (void *)f->mu, (void *)f->sig, (void *)f->loss})
+                    (void *)f->mu, (void *)f->L, (void *)f->cov, (void *)f->loss})
         if (p) cudaFree(p);
     if (f->h_grad) cudaFreeHost(f->h_grad);
     delete f;
@@ -938,24 +990,31 @@ lisa_status lisa_flow_get_weights(lisa_flow_t *f, float *w) {
     return LISA_OK;
 }
 
-lisa_status lisa_flow_set_standardisation(lisa_flow_t *f, const double *mu, const double *sigma) {
+lisa_status lisa_flow_set_whitening(lisa_flow_t *f, const double *mu, const double *L) {
     if (!f) return LISA_ERR_ARG;
-    if (!mu || !sigma) return ffail(f, LISA_ERR_ARG, "NULL standardisation");
-    for (int d = 0; d < FD; d++)
-        if (!std::isfinite(mu[d]) || !(sigma[d] > 0.0) || !std::isfinite(sigma[d]))
-            return ffail(f, LISA_ERR_ARG, "mu must be finite and sigma > 0");
+    if (!mu || !L) return ffail(f, LISA_ERR_ARG, "NULL whitening");
+    double Lc[FD * FD];
+    for (int i = 0; i < FD; i++) {
+        if (!std::isfinite(mu[i])) return ffail(f, LISA_ERR_ARG, "mu must be finite");
+        for (int j = 0; j < FD; j++) {
+            const double v = j <= i ? L[i * FD + j] : 0.0;
+            if (!std::isfinite(v)) return ffail(f, LISA_ERR_ARG, "L must be finite");
+            Lc[i * FD + j] = v;
+        }
+        if (!(Lc[i * FD + i] > 0.0)) return ffail(f, LISA_ERR_ARG, "L needs a positive diagonal");
+    }
     FCK(cudaSetDevice(f->device), "cudaSetDevice");
     FCK(cudaMemcpy(f->mu, mu, sizeof(double) * FD, cudaMemcpyHostToDevice), "upload");
-    FCK(cudaMemcpy(f->sig, sigma, sizeof(double) * FD, cudaMemcpyHostToDevice), "upload");
+    FCK(cudaMemcpy(f->L, Lc, sizeof(double) * FD * FD, cudaMemcpyHostToDevice), "upload");
     return LISA_OK;
 }
 
-lisa_status lisa_flow_get_standardisation(lisa_flow_t *f, double *mu, double *sigma) {
+lisa_status lisa_flow_get_whitening(lisa_flow_t *f, double *mu, double *L) {
     if (!f) return LISA_ERR_ARG;
     FCK(cudaSetDevice(f->device), "cudaSetDevice");
     FCK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     if (mu) FCK(cudaMemcpy(mu, f->mu, sizeof(double) * FD, cudaMemcpyDeviceToHost), "download");
-    if (sigma) FCK(cudaMemcpy(sigma, f->sig, sizeof(double) * FD, cudaMemcpyDeviceToHost), "download");
+    if (L) FCK(cudaMemcpy(L, f->L, sizeof(double) * FD * FD, cudaMemcpyDeviceToHost), "download");
     return LISA_OK;
 }
 

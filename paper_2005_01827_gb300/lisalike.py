@@ -41,7 +41,7 @@ SYMBOLS = (
     "lisa_sampler_get_flow", "lisa_sampler_flow_stats",
     # include/lisa_flow.h
     "lisa_flow_create", "lisa_flow_destroy", "lisa_flow_last_error", "lisa_flow_set_weights",
-    "lisa_flow_get_weights", "lisa_flow_set_standardisation", "lisa_flow_get_standardisation",
+    "lisa_flow_get_weights", "lisa_flow_set_whitening", "lisa_flow_get_whitening",
     "lisa_flow_normalize", "lisa_flow_generate", "lisa_flow_gradients", "lisa_flow_train",
 )
 FLOW_COUPLINGS, FLOW_HIDDEN, FLOW_PARAMS_PER_COUPLING = 8, 128, 20886
@@ -198,15 +198,15 @@ def load(path: str = LIB_PATH):
     L.lisa_flow_last_error.restype = C.c_char_p
     L.lisa_flow_set_weights.argtypes = [vp, vp]
     L.lisa_flow_get_weights.argtypes = [vp, vp]
-    L.lisa_flow_set_standardisation.argtypes = [vp, vp, vp]
-    L.lisa_flow_get_standardisation.argtypes = [vp, vp, vp]
+    L.lisa_flow_set_whitening.argtypes = [vp, vp, vp]
+    L.lisa_flow_get_whitening.argtypes = [vp, vp, vp]
     L.lisa_flow_normalize.argtypes = [vp, vp, i, vp, vp, vp]
     L.lisa_flow_generate.argtypes = [vp, vp, i, vp, vp, vp]
     L.lisa_flow_gradients.argtypes = [vp, vp, i, vp, dp, vp]
     L.lisa_flow_train.argtypes = [vp, vp, i64, i, i, d, u64, u32, vp, vp]
     for fn in ("lisa_sampler_enable_flow", "lisa_sampler_flow_stats", "lisa_flow_create",
-               "lisa_flow_set_weights", "lisa_flow_get_weights", "lisa_flow_set_standardisation",
-               "lisa_flow_get_standardisation", "lisa_flow_normalize", "lisa_flow_generate",
+               "lisa_flow_set_weights", "lisa_flow_get_weights", "lisa_flow_set_whitening",
+               "lisa_flow_get_whitening", "lisa_flow_normalize", "lisa_flow_generate",
                "lisa_flow_gradients", "lisa_flow_train"):
         getattr(L, fn).restype = i
     for fn in ("lisa_sampler_create", "lisa_sampler_set_ladder", "lisa_sampler_set_state",
@@ -735,14 +735,19 @@ class Flow:
         _fcheck(load().lisa_flow_get_weights(self.h, _ptr(p)), self.h)
         return unpack_flow_weights(p)
 
-    def set_standardisation(self, mu, sig):
-        m, s_ = _f64(mu), _f64(sig)
-        _fcheck(load().lisa_flow_set_standardisation(self.h, _ptr(m), _ptr(s_)), self.h)
+    def set_whitening(self, mu, L):
+        """mu [11]; L [11, 11] lower triangular, or a vector of scales (diagonal L)."""
+        m = _f64(mu)
+        Lm = np.asarray(L, dtype=np.float64)
+        Lm = _f64(np.diag(Lm) if Lm.ndim == 1 else Lm)
+        _fcheck(load().lisa_flow_set_whitening(self.h, _ptr(m), _ptr(Lm)), self.h)
 
-    def standardisation(self):
-        m, s_ = np.empty(SAMPLER_NDIM), np.empty(SAMPLER_NDIM)
-        _fcheck(load().lisa_flow_get_standardisation(self.h, _ptr(m), _ptr(s_)), self.h)
-        return m, s_
+    set_standardisation = set_whitening
+
+    def whitening(self):
+        m, Lm = np.empty(SAMPLER_NDIM), np.empty((SAMPLER_NDIM, SAMPLER_NDIM))
+        _fcheck(load().lisa_flow_get_whitening(self.h, _ptr(m), _ptr(Lm)), self.h)
+        return m, Lm
 
     def _dev(self, a):
         import torch
