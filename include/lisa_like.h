@@ -211,6 +211,38 @@ void lisa_like_destroy(lisa_like_t *h);
  * on this thread. */
 const char *lisa_like_last_error(const lisa_like_t *h);
 
+/* ------------------------------------------------------------------ relative binning
+ * A cheaper approximation of the same ln L, which the paper leaves as future work
+ * (Sec. II.A): relative binning (Zackay, Dai & Venumadhav 2018), the heterodyning of
+ * Cornish (2010).  A fiducial waveform h0 (parameters near the posterior) fixes coarse
+ * bins -- n_rb + 1 edges log-spaced in frequency over the union of its mode bands,
+ * snapped to the grid, plus every mode's band start and end + 1 -- and per-bin summary
+ * data of every mode lm, channel c and bin b (w = 4 df / S, Eq. (3)):
+ *   A0 = sum w d h0_lm*,  A1 = sum w d h0_lm* (f - f_b),
+ *   B0 = sum w h0_lm h0_l'm'*,  B1 = sum w h0_lm h0_l'm'* (f - f_b)  (mode pairs).
+ * A template's modes are then evaluated only at the edges (waveform and response at each
+ * edge frequency, no spline); their ratios to h0 are linear across each bin (held
+ * constant across a bin where h0 vanishes at one edge), and <d|h>, <h|h>, ln L follow from
+ * the summary data.  Exact at the fiducial and for templates whose ratio to it is
+ * constant; the error grows as the square of the bin width.
+ *
+ * lisa_like_set_fiducial: summary data for `params` [11] (host) with n_rb in [8, 256]
+ * coarse bins, on the data of the last lisa_like_set_data (set_data discards them).
+ * Synchronous.  Errors: LISA_ERR_STATE without data, LISA_ERR_ARG for invalid
+ * parameters or a fiducial with no active mode. */
+lisa_status lisa_like_set_fiducial(lisa_like_t *h, const double *params, int n_rb);
+
+/* The bin edges as grid indices (edges may be NULL to query *n_edges). */
+lisa_status lisa_like_rb_edges(lisa_like_t *h, int64_t *edges, int *n_edges);
+
+/* ln L, <d|h>, <h|h> by relative binning for B walkers (host buffers, blocking; dh, hh may
+ * be NULL).  Invalid walkers: -inf, 0, 0. */
+lisa_status lisa_like_loglike_rb(lisa_like_t *h, const double *params, int B, double *lnL,
+                                 double *dh, double *hh);
+/* The same on device pointers, enqueued on `stream` (NULL = default stream). */
+lisa_status lisa_like_loglike_rb_device(lisa_like_t *h, const double *d_params, int B,
+                                        double *d_lnL, double *d_dh, double *d_hh, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,8 @@ struct DenseTune {
 __host__ __device__ inline int n_groups(int B, int G) { return (B + G - 1) / G; }
 
 cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s);
+// the band kernel alone (walker constants, peak, bands; no knots)
+cudaError_t launch_band(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, int group,
                         cudaStream_t s);

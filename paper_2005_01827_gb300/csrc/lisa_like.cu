@@ -73,6 +73,7 @@ struct lisa_like {
     // tile shapes chosen by lisa_like_autotune, per (n_bins, K, precision)
     std::map<std::tuple<int, int, int>, DenseTune> tuned;
     bool profiling = false;
+    lisa::RbState *rb = nullptr;       // relative binning (lisa_like_set_fiducial)
     std::vector<cudaEvent_t> prof_ev;  // kProfEvents events per profiled call
     int prof_calls = 0;
     std::string err;
@@ -353,6 +354,37 @@ LikeInfo like_info(const lisa_like_t *h) {
     return i;
 }
 
+LikeCore like_core(lisa_like_t *h) {
+    LikeCore c;
+    c.stream = h->stream;
+    c.device = h->device;
+    c.max_batch = h->max_batch;
+    c.have_data = h->have_data ? 1 : 0;
+    c.N = h->N;
+    c.L = h->L;
+    c.K = h->K;
+    c.t0 = h->t0;
+    c.f0 = h->f0;
+    c.df = h->df;
+    c.dd = h->dd;
+    c.timeout_s = h->timeout_s;
+    for (int i = 0; i < 6; i++) {
+        c.ml[i] = h->ml[i];
+        c.mm[i] = h->mm[i];
+    }
+    c.bins = h->bins;
+    c.params = h->params;
+    c.h_params = h->h_params;
+    c.out = h->out;
+    c.h_out = h->h_out;
+    c.stage = bufs_of(h, h->params);
+    return c;
+}
+
+RbState *&like_rb(lisa_like_t *h) { return h->rb; }
+lisa_status like_fail(lisa_like_t *h, lisa_status st, const std::string &msg) { return fail(h, st, msg); }
+lisa_status like_wait(lisa_like_t *h, cudaStream_t s) { return wait_for(h, s); }
+
 lisa_status like_enqueue(lisa_like_t *h, const double *d_params, int B, double *d_lnL,
                          cudaStream_t s, int *launches) {
     if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
@@ -580,6 +612,10 @@ lisa_status lisa_like_set_data(lisa_like_t *h, double f0, double df, int64_t n_b
     if (h->bins) cudaFree(h->bins);
     if (h->bins32) cudaFree(h->bins32);
     if (h->part) cudaFree(h->part);
+    if (h->rb) {  // summary data belong to the previous data
+        lisa::rb_free(h->rb);
+        h->rb = nullptr;
+    }
     h->bins = bins;
     h->bins32 = bins32;
     h->part = part;
@@ -869,6 +905,7 @@ void lisa_like_destroy(lisa_like_t *h) {
     if (h->bins) cudaFree(h->bins);
     if (h->bins32) cudaFree(h->bins32);
     if (h->part) cudaFree(h->part);
+    lisa::rb_free(h->rb);
     drop_graph(h);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);

@@ -125,6 +125,11 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
     }
 }
 
+cudaError_t launch_band(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    band_kernel<<<(d.B * d.L + 127) / 128, 128, 0, s>>>(d, b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s) {
     band_kernel<<<(d.B * d.L + 127) / 128, 128, 0, s>>>(d, b);
     cudaError_t e = cudaGetLastError();

@@ -30,7 +30,8 @@ SYMBOLS = (
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
     "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
-    "lisa_like_mode_inner",
+    "lisa_like_mode_inner", "lisa_like_set_fiducial", "lisa_like_rb_edges",
+    "lisa_like_loglike_rb", "lisa_like_loglike_rb_device",
     # include/lisa_sampler.h
     "lisa_sampler_default_config", "lisa_sampler_create", "lisa_sampler_set_ladder",
     "lisa_sampler_set_state", "lisa_sampler_run", "lisa_sampler_get_state",
@@ -159,6 +160,13 @@ def load(path: str = LIB_PATH):
     L.lisa_like_autotune.restype = i
     L.lisa_like_mode_inner.argtypes = [vp, vp, i, vp, vp]
     L.lisa_like_mode_inner.restype = i
+    L.lisa_like_set_fiducial.argtypes = [vp, vp, i]
+    L.lisa_like_rb_edges.argtypes = [vp, vp, ip]
+    L.lisa_like_loglike_rb.argtypes = [vp, vp, i, vp, vp, vp]
+    L.lisa_like_loglike_rb_device.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    for fn in ("lisa_like_set_fiducial", "lisa_like_rb_edges", "lisa_like_loglike_rb",
+               "lisa_like_loglike_rb_device"):
+        getattr(L, fn).restype = i
     L.lisa_like_last_launches.argtypes = [vp]
     L.lisa_like_last_launches.restype = i
     L.lisa_like_destroy.argtypes = [vp]
@@ -435,6 +443,27 @@ class LisaLike:
 
     def last_launches(self):
         return lisa_like_last_launches(self.h)
+
+    def set_fiducial(self, params, n_rb=256):
+        """Relative-binning summary data about the fiducial `params` [11]."""
+        p = _f64(params)
+        _check(load().lisa_like_set_fiducial(self.h, _ptr(p), int(n_rb)), self.h)
+
+    def rb_edges(self):
+        n = C.c_int()
+        _check(load().lisa_like_rb_edges(self.h, None, C.byref(n)), self.h)
+        e = np.empty(n.value, dtype=np.int64)
+        _check(load().lisa_like_rb_edges(self.h, _ptr(e), C.byref(n)), self.h)
+        return e
+
+    def loglike_rb(self, params):
+        """ln L, <d|h>, <h|h> by relative binning (after set_fiducial)."""
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        lnL, dh, hh = np.empty(B), np.empty(B), np.empty(B)
+        _check(load().lisa_like_loglike_rb(self.h, _ptr(p), B, _ptr(lnL), _ptr(dh), _ptr(hh)),
+               self.h)
+        return lnL, dh, hh
 
 
 def dl_from_z(z):
