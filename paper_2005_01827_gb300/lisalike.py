@@ -273,6 +273,12 @@ def lisa_like_loglike_device(h, d_params, B, d_lnL, d_dh=None, d_hh=None, stream
                                            _ptr(d_hh), s), h)
 
 
+def lisa_like_loglike_rb_device(h, d_params, B, d_lnL, d_dh=None, d_hh=None, stream=None):
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(load().lisa_like_loglike_rb_device(h, _ptr(d_params), B, _ptr(d_lnL), _ptr(d_dh),
+                                              _ptr(d_hh), s), h)
+
+
 def lisa_like_data_inner(h) -> float:
     v = C.c_double()
     _check(load().lisa_like_data_inner(h, C.byref(v)), h)
