@@ -127,6 +127,11 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
             r.kb0 = kb0;
             r.invw = 1.0f / (float)W;
             r.pad[0] = r.pad[1] = 0;
+            if (s == 0) {  // the (walker, mode)'s segment-guess constants, read once per tile
+                const double f_lo = b.fedge[2 * wm], f_hi = b.fedge[2 * wm + 1];
+                r.pad[0] = __float_as_int((float)f_lo);
+                r.pad[1] = __float_as_int((float)((double)(K - 1) / log2(f_hi / f_lo)));
+            }
             segs[g] = r;
         } else {
             ulonglong2 *o = reinterpret_cast<ulonglong2 *>(phases + (size_t)kPhaseWords * g);
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
     __shared__ float2 tab[256];
     __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
     __shared__ float s_flo[G][kMaxModes], s_scl[G][kMaxModes];
-    __shared__ double red[G][2][4];  // per slot, per warp partial sums
+    __shared__ float4 red[G][4];  // per slot, per warp: (ri, ri comp, hh, hh comp)
     __shared__ int s_skip[G];
     const int tid = threadIdx.x;
     for (int k = tid; k < 256; k += blockDim.x) {
@@ -323,9 +328,9 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 if (b.valid[w] && bd[0]) {
                     lo = bd[1];
                     hi = bd[2];
-                    const double f_lo = b.fedge[2 * wm], f_hi = b.fedge[2 * wm + 1];
-                    flo = (float)f_lo;
-                    scl = (float)((double)(K - 1) / log2(f_hi / f_lo));
+                    const int2 pv = __ldg(reinterpret_cast<const int2 *>(segs[wm * (K - 1)].pad));
+                    flo = __int_as_float(pv.x);
+                    scl = __int_as_float(pv.y);
                 }
             }
             s_lo[k][mi] = lo;
@@ -459,21 +464,30 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
             float rl = -rc, hl = -hc;
             warp_sum_pair(rs, rl);
             warp_sum_pair(hs, hl);
-            if ((tid & 31) == 0) {
-                red[k][0][tid >> 5] = (double)rs + (double)rl;
-                red[k][1][tid >> 5] = (double)hs + (double)hl;
-            }
+            if ((tid & 31) == 0) red[k][tid >> 5] = make_float4(rs, rl, hs, hl);
         }
-        // one block barrier per item: thread k sums slot k over the warps
+        // one block barrier per item: thread k sums slot k over the warps, error-free
+        // in FP32 (two-sum of the values, compensations added), then once to FP64
         __syncthreads();
         if (tid < G && s_walker[tid] >= 0) {
             const size_t slot = (size_t)item * G + tid;
             double a = 0.0, c = 0.0;
-            if (!s_skip[tid])
-                for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
-                    a += red[tid][0][q];
-                    c += red[tid][1][q];
+            if (!s_skip[tid]) {
+                float4 v = red[tid][0];
+                float as = v.x, ae = v.y, cs = v.z, ce = v.w;
+                for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+                    v = red[tid][q];
+                    float t, e;
+                    two_sum(as, v.x, t, e);
+                    as = t;
+                    ae += e + v.y;
+                    two_sum(cs, v.z, t, e);
+                    cs = t;
+                    ce += e + v.w;
                 }
+                a = (double)as + (double)ae;
+                c = (double)cs + (double)ce;
+            }
             b.part[2 * slot] = a;
             b.part[2 * slot + 1] = c;
         }
