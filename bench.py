@@ -49,10 +49,13 @@ FLOP_BIN = 29
 # data bytes streamed per bin by a walker tile (w and w*d for A, E, T, FP64) and the
 # spline coefficients per segment (8 series x 4 doubles)
 BYTES_BIN = 72
-# DRAM bytes per (walker, bin) of dense_f64_kernel<8, 8> from one ncu capture of 32
-# walkers (dram__bytes_read.sum + dram__bytes_write.sum = 751.3 MB over 69,589,136
-# walker-bins); scaled to a launch by its walker-bins.  None once the kernel changes.
-TRAFFIC_F64_PER_WALKER_BIN = 751.3e6 / 69589136
+# DRAM bytes per (walker, bin) of the dense kernels from ncu captures of 32 walkers
+# (dram__bytes_read.sum + dram__bytes_write.sum over 69,589,136 walker-bins), per tile
+# shape (bins per thread, group); scaled to a launch by its walker-bins.  A shape without
+# a capture reports null.
+TRAFFIC_F64_PER_WALKER_BIN = {(8, 8): (753.95e6 + 4.90e6) / 69589136,
+                              (4, 8): (754.31e6 + 6.07e6) / 69589136}
+TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (375.78e6 + 4.63e6) / 69589136}
 
 
 def peaks():
@@ -278,6 +281,8 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     make_inputs(lisalike, like, g, 1, 1)          # same data as the FP64 handle
     if not args.no_autotune:
         lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    if args.tile:
+        lisalike.lisa_like_set_tune(like.h, *[int(v) for v in args.tile.split(",")])
     dparams = torch.tensor(th, dtype=torch.float64, device="cuda")
     lnL = torch.empty(B, dtype=torch.float64, device="cuda")
 
@@ -306,11 +311,14 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
+    tpw = TRAFFIC_SPLIT_PER_WALKER_BIN.get(tuple(shape[:2]))
     return {"value": job_value(world, B, args.steps, ms), "unit": "evals/s",
             "ms_per_step": ms / args.steps, "dtype": "f32+f64", "graphs": graphs,
             "tile": {"bins_per_thread": shape[0], "group": shape[1], "blocks": shape[2]},
             "roofline": {"bound": "alu", "kernel": "dense_split_kernel", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": tpw * bins if tpw else None,
+                         "traffic_unit": "bytes per launch",
                          "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
                          "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
                                                zip(("knots", "splines", "segprep", "plan",
@@ -761,6 +769,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape (8 bins per thread, groups of 8); for "
                          "profiling captures that must see one known kernel variant")
+    ap.add_argument("--tile", default=None,
+                    help="P,G: force the dense kernels' tile shape (bins per thread, walker "
+                         "group) after autotuning; for profiling captures of that variant")
     ap.add_argument("--train-every", type=int, default=500,
                     help="flow workload: steps between flow trainings (500 is the workload; "
                          "smaller only for profiling captures)")
@@ -791,6 +802,8 @@ def main():
     # tile shapes from the autotuner (timed on a 256-walker sample of the workload)
     if not args.no_autotune:
         lisalike.lisa_like_autotune(like.h, th[:256], min(256, B))
+    if args.tile:
+        lisalike.lisa_like_set_tune(like.h, *[int(v) for v in args.tile.split(",")])
 
     # a dedicated stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
@@ -855,7 +868,8 @@ def main():
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
-    traffic = TRAFFIC_F64_PER_WALKER_BIN * bins if shape[:2] == (8, 8) else None
+    tpw = TRAFFIC_F64_PER_WALKER_BIN.get(tuple(shape[:2]))
+    traffic = tpw * bins if tpw else None
     roofline = {"bound": "alu", "kernel": "dense_f64_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
