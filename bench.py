@@ -319,6 +319,14 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": tpw * bins if tpw else None,
                          "traffic_unit": "bytes per launch",
+                         "fractions": {
+                             "binding": "fp32 (issue)", "fp32": achieved / peak,
+                             "fp64": None, "mufu": None,
+                             "hbm": (tpw * bins / (dense_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"])
+                             if (tpw and peaks().get("hbm_gbs")) else None,
+                             "note": "fp64: per-item set-up only; mufu: one log2 per chunk "
+                                     "(the phasor is a table and polynomials); ncu: issue 63 %, "
+                                     "FMA pipe 43 %, ALU 28 %"},
                          "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
                          "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
                                                zip(("knots", "splines", "segprep", "plan",
@@ -389,6 +397,9 @@ def sampler_setup(args, rank, local):
     xc = LL.from_physical(inj, True, W.T0_YEAR)
     scale = np.array([1e-3, 1e-3, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2, 1e-3, 1e-3, 1e-2, 1e-4])
     x0 = LL.sky_mode_init(xc, scale, list(cfg.lower), list(cfg.upper), T, Wk, 7 + rank)
+    if getattr(args, "start", "sky-modes") == "true-mode":
+        # every walker at the injection's own sky mode (jitter only)
+        x0[:, :, 7:9] = xc[7:9] + scale[7:9] * np.random.default_rng(5 + rank).standard_normal((T, Wk, 2))
     # tile shapes from the autotuner, timed on the starting walkers
     dx = torch.tensor(x0.reshape(-1, 11)[: T * Wk // 2], dtype=torch.float64, device="cuda")
     dth = torch.empty_like(dx)
@@ -535,6 +546,7 @@ def run_flow(args, world, rank, local):
 
     LL, like, stream, x0, prec = sampler_setup(args, rank, local)
     T, Wk = W.SAMPLER_T, W.SAMPLER_W
+    xc7 = float(np.median(x0[0, :, 7]))  # reference longitude for the mode quarters
     every = args.train_every
     burn = max(args.warmup, 2 * every)
     K = args.steps
@@ -565,7 +577,14 @@ def run_flow(args, world, rank, local):
         acc1, _ = s.counts()
         taus, tau = chain_stats(LL, chain, K, Wk, stream)
         c = chain.cpu().numpy().reshape(-1, 11)
-        r = {"ms_per_step": ms / K, "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
+        # the dominant longitude mode (lambda_L within pi/4 of the median of the samples
+        # nearest the most populated quarter-turn)
+        quarter = np.floor(((c[:, 7] - xc7) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4
+        dom = int(np.bincount(quarter.astype(int), minlength=4).argmax())
+        main = c[quarter == dom]
+        r = {"ms_per_step": ms / K,
+             "dominant_mode_fraction": float(main.shape[0] / c.shape[0]),
+             "mean_dominant": main.mean(axis=0).tolist(), "std_dominant": main.std(axis=0).tolist(), "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
              "ess": K * Wk / tau, "ess_per_s": world * K * Wk / tau / (ms * 1e-3),
              "stretch_acceptance_cold": float((acc1 - acc0)[0, 0] / max((acc1 - acc0)[0, 1], 1)),
              "burn_in_s": burn_s, "launches_per_step": s.step_launches(),
@@ -583,15 +602,21 @@ def run_flow(args, world, rank, local):
     like.close()
     p, f = out["plain"], out["flow"]
     sd = np.array(p["std"])
+    sdd = np.array(p["std_dominant"])
     accuracy = {"max_abs_mean_diff_over_std": float(np.max(np.abs(np.array(f["mean"]) -
                                                                    np.array(p["mean"])) / sd)),
                 "std_ratio_range": [float(np.min(np.array(f["std"]) / sd)),
-                                    float(np.max(np.array(f["std"]) / sd))]}
+                                    float(np.max(np.array(f["std"]) / sd))],
+                "dominant_mode": {
+                    "max_abs_mean_diff_over_std": float(np.max(np.abs(
+                        np.array(f["mean_dominant"]) - np.array(p["mean_dominant"])) / sdd)),
+                    "std_ratio_range": [float(np.min(np.array(f["std_dominant"]) / sdd)),
+                                        float(np.max(np.array(f["std_dominant"]) / sdd))]}}
     line = {"metric": FLOW_METRIC, "value": f["ess_per_s"], "unit": "effective samples/s",
             "n_gpus": world, "steps": K, "warmup": burn, "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == LL.LISA_PREC_SPLIT else "f64", "data": "synthetic",
-            "config": {"workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
+            "config": {"start": args.start, "workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
                        "(11-128-128-22, bf16 mma.sync, FP32 accumulate), trained every 500 "
                        "steps on the coldest chain until the end of burn-in, independence MH "
                        "on the coldest temperature every step",
@@ -769,6 +794,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape (8 bins per thread, groups of 8); for "
                          "profiling captures that must see one known kernel variant")
+    ap.add_argument("--start", default="sky-modes", choices=["sky-modes", "true-mode"],
+                    help="sampler workloads: walkers at the 8 LISA-frame sky modes (default) or "
+                         "all at the injection's own sky mode")
     ap.add_argument("--tile", default=None,
                     help="P,G: force the dense kernels' tile shape (bins per thread, walker "
                          "group) after autotuning; for profiling captures of that variant")
@@ -880,6 +908,12 @@ def main():
                                            "finish"), stage_ms)},
                 "hbm_gbs": BYTES_BIN * bins / (dense_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks().get("hbm_gbs")}
+    hbm_peak = peaks().get("hbm_gbs")
+    roofline["fractions"] = {
+        "binding": "fp64", "fp64": achieved / peak, "fp32": 0.0, "mufu": 0.0,
+        "hbm": (traffic / (dense_ms * 1e-3) / 1e9 / hbm_peak) if (traffic and hbm_peak) else None,
+        "note": "fp32 and mufu: the FP64 kernel's inner loop issues neither (ncu: FMA pipe "
+                "0.7 %, XU ~0 %); hbm: measured DRAM bytes per launch over the launch time"}
     if c3:
         roofline["note"] = "stage times from one profiled call before graph replay"
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,

@@ -211,6 +211,16 @@ void lisa_like_destroy(lisa_like_t *h);
  * on this thread. */
 const char *lisa_like_last_error(const lisa_like_t *h);
 
+/* The mode-pair inner products Re<h_lm|h_l'm'> of B walkers (host params [B][11]),
+ * cross [B][L][L] (host, symmetric; the diagonal is <h_lm|h_lm>).  With the per-mode
+ * <d|h_lm> of lisa_like_mode_inner, ln L = sum_lm <d|h_lm> - 1/2 sum <h_lm|h_l'm'>
+ * - <d|d>/2: the mode-by-mode form with cross terms that the paper contrasts with its
+ * single combined data stream (Sec. II.A), and the reason the total SNR of Table III is
+ * not the quadrature sum of the mode SNRs.  Computed from the template of every mode
+ * and mode pair: Re<h_a|h_b> = (<h_a + h_b|h_a + h_b> - <h_a|h_a> - <h_b|h_b>) / 2
+ * (L (L + 1) / 2 likelihood passes).  Blocking. */
+lisa_status lisa_like_mode_cross(lisa_like_t *h, const double *params, int B, double *cross);
+
 /* ------------------------------------------------------------------ relative binning
  * A cheaper approximation of the same ln L, which the paper leaves as future work
  * (Sec. II.A): relative binning (Zackay, Dai & Venumadhav 2018), the heterodyning of

@@ -246,7 +246,7 @@ bool make_tune(const lisa_like_t *h, int per_thread, int group, DenseTune *t) {
 }
 
 lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
-                    double *hh, cudaStream_t s, bool profile, int only_mode = -1);
+                    double *hh, cudaStream_t s, bool profile, unsigned mode_mask = 0);
 
 void drop_graph(lisa_like_t *h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -294,9 +294,10 @@ lisa_status run_all(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     return LISA_OK;
 }
 
-// the call's kernels on stream s; only_mode >= 0 restricts the template to that one mode
+// the call's kernels on stream s; a non-zero mode_mask restricts the template to the modes
+// whose bits are set (bit i = the handle's mode i)
 lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, double *dh,
-                    double *hh, cudaStream_t s, bool profile, int only_mode) {
+                    double *hh, cudaStream_t s, bool profile, unsigned mode_mask) {
     cudaEvent_t *ev = nullptr;
     if (profile) {
         if (h->prof_calls >= 4096) return fail(h, LISA_ERR_STATE, "read the profile first");
@@ -306,10 +307,15 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     }
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     StageDims d = dims_of(h, B);
-    if (only_mode >= 0) {
-        d.L = 1;
-        d.ml[0] = h->ml[only_mode];
-        d.mm[0] = h->mm[only_mode];
+    if (mode_mask) {
+        int n = 0;
+        for (int i = 0; i < h->L; i++)
+            if ((mode_mask >> i) & 1u) {
+                d.ml[n] = h->ml[i];
+                d.mm[n] = h->mm[i];
+                n++;
+            }
+        d.L = n;
     }
     const StageBufs b = bufs_of(h, dparams);
     const int tile = h->tune.threads * h->tune.per_thread;
@@ -869,7 +875,8 @@ lisa_status lisa_like_mode_inner(lisa_like_t *h, const double *params, int B, do
     const int L = h->L;
     std::vector<double> buf((size_t)2 * B * L);
     for (int mi = 0; mi < L; mi++) {
-        lisa_status st = enqueue(h, h->params, B, h->out, h->out + B, h->out + 2 * B, s, false, mi);
+        lisa_status st = enqueue(h, h->params, B, h->out, h->out + B, h->out + 2 * B, s, false,
+                                 1u << mi);
         if (st != LISA_OK) return st;
         LCK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s),
             "result download");
@@ -885,6 +892,46 @@ lisa_status lisa_like_mode_inner(lisa_like_t *h, const double *params, int B, do
     }
     if (dh_modes) std::memcpy(dh_modes, buf.data(), sizeof(double) * B * L);
     if (hh_modes) std::memcpy(hh_modes, buf.data() + (size_t)B * L, sizeof(double) * B * L);
+    return LISA_OK;
+}
+
+lisa_status lisa_like_mode_cross(lisa_like_t *h, const double *params, int B, double *cross) {
+    if (!h) return LISA_ERR_ARG;
+    if (!h->have_data) return fail(h, LISA_ERR_STATE, "set_data must be called first");
+    if (B < 1 || B > h->max_batch || !params || !cross)
+        return fail(h, LISA_ERR_ARG, "bad batch or NULL output");
+    LCK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = h->stream;
+    LCK(cudaMemcpyAsync(h->params, params, sizeof(double) * kNPar * B, cudaMemcpyHostToDevice, s),
+        "parameter upload");
+    const int L = h->L;
+    // <h_a + h_b | h_a + h_b> for every pair (a single mode when a = b), then
+    // Re<h_a|h_b> = (<h_a+b|h_a+b> - <h_a|h_a> - <h_b|h_b>) / 2
+    std::vector<double> pair((size_t)L * L * B);
+    for (int a = 0; a < L; a++)
+        for (int b = a; b < L; b++) {
+            const unsigned mask = (1u << a) | (1u << b);
+            lisa_status st = enqueue(h, h->params, B, h->out, h->out + B, h->out + 2 * B, s,
+                                     false, mask);
+            if (st != LISA_OK) return st;
+            LCK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s),
+                "result download");
+            LCK(cudaMemcpyAsync(h->h_err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s),
+                "result download");
+            st = wait_for(h, s);
+            if (st != LISA_OK) return st;
+            if (*h->h_err) return fail(h, LISA_ERR_TIMEOUT, "a device wait for staged data gave up");
+            for (int w = 0; w < B; w++) pair[((size_t)a * L + b) * B + w] = h->h_out[2 * B + w];
+        }
+    for (int w = 0; w < B; w++)
+        for (int a = 0; a < L; a++)
+            for (int b = 0; b < L; b++) {
+                const int lo = a < b ? a : b, hi = a < b ? b : a;
+                double v = pair[((size_t)lo * L + hi) * B + w];
+                if (lo != hi)
+                    v = 0.5 * (v - pair[((size_t)lo * L + lo) * B + w] - pair[((size_t)hi * L + hi) * B + w]);
+                cross[((size_t)w * L + a) * L + b] = v;
+            }
     return LISA_OK;
 }
 

@@ -30,7 +30,7 @@ SYMBOLS = (
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
     "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
-    "lisa_like_mode_inner", "lisa_like_set_fiducial", "lisa_like_rb_edges",
+    "lisa_like_mode_inner", "lisa_like_mode_cross", "lisa_like_set_fiducial", "lisa_like_rb_edges",
     "lisa_like_loglike_rb", "lisa_like_loglike_rb_device",
     # include/lisa_sampler.h
     "lisa_sampler_default_config", "lisa_sampler_create", "lisa_sampler_set_ladder",
@@ -160,6 +160,8 @@ def load(path: str = LIB_PATH):
     L.lisa_like_autotune.restype = i
     L.lisa_like_mode_inner.argtypes = [vp, vp, i, vp, vp]
     L.lisa_like_mode_inner.restype = i
+    L.lisa_like_mode_cross.argtypes = [vp, vp, i, vp]
+    L.lisa_like_mode_cross.restype = i
     L.lisa_like_set_fiducial.argtypes = [vp, vp, i]
     L.lisa_like_rb_edges.argtypes = [vp, vp, ip]
     L.lisa_like_loglike_rb.argtypes = [vp, vp, i, vp, vp, vp]
@@ -449,6 +451,14 @@ class LisaLike:
 
     def last_launches(self):
         return lisa_like_last_launches(self.h)
+
+    def mode_cross(self, params):
+        """Re<h_a|h_b> for every pair of modes, array [B, n_modes, n_modes]."""
+        p = _f64(np.atleast_2d(params))
+        B = p.shape[0]
+        out = np.empty((B, self.L, self.L))
+        _check(load().lisa_like_mode_cross(self.h, _ptr(p), B, _ptr(out)), self.h)
+        return out
 
     def set_fiducial(self, params, n_rb=256):
         """Relative-binning summary data about the fiducial `params` [11]."""

@@ -67,3 +67,39 @@ def test_table3_breakdown_with_the_stand_in(pkg, orc):
     b1 = np.sqrt(hhm[0])
     assert np.argsort(-b1).tolist() == [0, 1, 2, 3, 4, 5]
     assert 300 < math.sqrt(hh[0]) < 1200
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mode_cross_terms_match_the_oracle_and_rebuild_lnl(pkg, orc, prec):
+    """Re<h_a|h_b> of every mode pair against the oracle's single-mode templates; with
+    <d|h_a> it rebuilds ln L exactly (the mode-by-mode form with cross terms); the cross
+    terms are why the total SNR is not the quadrature sum of the mode SNRs (Table III)."""
+    g = W.GRID_C2
+    S = orc.psd_aet(g.freqs())
+    inj = W.theta_table2(1)
+    d = orc.template(inj, W.T0_YEAR, W.MODES6, 1024, g.f0, g.df, g.n_bins)
+    d = d + orc.noise(S, g.df, W.white_noise(g.n_bins, 2))
+    th = np.vstack([inj, W.theta_table2(6)])
+    like = pkg.LisaLike(modes=W.MODES6, n_knots=1024, max_batch=4, precision=prec)
+    like.set_data(g.f0, g.df, g.n_bins, d, S)
+    X = like.mode_cross(th)
+    dhm, hhm = like.mode_inner(th)
+    lnL, dh, hh = like.loglike(th)
+    dd = like.data_inner()
+    like.close()
+    tol = 1e-9 if prec == 0 else 1e-6
+    for b in range(2):
+        assert np.allclose(X[b], X[b].T, rtol=0, atol=0)
+        assert np.allclose(np.diag(X[b]), hhm[b], rtol=0, atol=tol * hh[b])
+        assert abs(X[b].sum() - hh[b]) <= tol * hh[b]
+        rebuilt = dhm[b].sum() - 0.5 * X[b].sum() - 0.5 * dd
+        assert abs(rebuilt - lnL[b]) <= tol * max(hh[b], dd)
+        hs = [orc.template(th[b], W.T0_YEAR, [md], 1024, g.f0, g.df, g.n_bins) for md in W.MODES6]
+        for a in range(6):
+            for c in range(a + 1, 6):
+                ref = orc.inner(hs[a], hs[c], S, g.df)
+                assert abs(X[b, a, c] - ref) <= 1e-6 * hh[b], (b, a, c, X[b, a, c], ref)
+    off = X[0].sum() - np.trace(X[0])
+    print("Binary 1: SNR %.1f, quadrature sum of mode SNRs %.1f, cross terms %.3e of <h|h>"
+          % (np.sqrt(hh[0]), np.sqrt(np.trace(X[0])), off / hh[0]))
+    assert abs(off) > 1e-6 * hh[0]
