@@ -149,74 +149,117 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 // scratch rows next to the second derivatives.
 constexpr int kSplineSystems = 32;
 
+// The three serial recurrences (factorisation, forward and backward sweeps) load their
+// inputs in chunks of kChunk knots ahead of the dependent arithmetic, so that the loads of
+// a chunk are in flight together instead of one per step; the arithmetic is unchanged.
+constexpr int kChunk = 8;
+
 __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
     const int K = d.K, n = K;
     const int nsys = d.B * d.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = blockIdx.x * kSplineSystems + lane;
     const bool mine = wm < nsys && b.band[(size_t)wm * 3];
-    const double *x = b.fk + (size_t)wm * K;
+    const double *__restrict__ x = b.fk + (size_t)wm * K;
     double *Mv = b.mscratch + (size_t)wm * kScratchRows * K;
-    double *ih = Mv + (size_t)kNSeries * K;  // 1 / h
-    double *dinv = ih + K;                   // 1 / pivot
-    double *cpr = dinv + K;                  // normalised super-diagonal
+    double *__restrict__ ih = Mv + (size_t)kNSeries * K;  // 1 / h
+    double *__restrict__ dinv = ih + K;                   // 1 / pivot
+    double *__restrict__ cpr = dinv + K;                  // normalised super-diagonal
     if (warp == 0 && mine) {
         double hprev = x[1] - x[0], hcur;
         const double ih0 = 1.0 / hprev;
         ih[0] = ih0;
         double cprev = 0.0;
         double ihprev = ih0;  // 1 / h_{i-1}
-        for (int i = 1; i <= n - 2; i++) {
-            hcur = x[i + 1] - x[i];
-            const double ihc = 1.0 / hcur;
-            ih[i] = ihc;
-            double dia = 2.0 * (hprev + hcur);
-            double sup = hcur;
-            double sb = hprev;
-            if (i == 1) {
-                dia += hprev * (hprev + hcur) * ihc;
-                sup -= hprev * hprev * ihc;
+        double xi = x[1];
+        for (int i0 = 1; i0 <= n - 2; i0 += kChunk) {
+            double xn[kChunk];
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) xn[k] = (i0 + k <= n - 2) ? x[i0 + k + 1] : 0.0;
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) {
+                const int i = i0 + k;
+                if (i > n - 2) break;
+                hcur = xn[k] - xi;
+                xi = xn[k];
+                const double ihc = 1.0 / hcur;
+                ih[i] = ihc;
+                double dia = 2.0 * (hprev + hcur);
+                double sup = hcur;
+                double sb = hprev;
+                if (i == 1) {
+                    dia += hprev * (hprev + hcur) * ihc;
+                    sup -= hprev * hprev * ihc;
+                }
+                if (i == n - 2) {
+                    dia += hcur * (hprev + hcur) * ihprev;
+                    sb -= hcur * hcur * ihprev;
+                }
+                const double pv = (i == 1) ? dia : dia - sb * cprev;
+                const double inv = 1.0 / pv;
+                dinv[i] = inv;
+                cprev = sup * inv;
+                cpr[i] = cprev;
+                hprev = hcur;
+                ihprev = ihc;
             }
-            if (i == n - 2) {
-                dia += hcur * (hprev + hcur) * ihprev;
-                sb -= hcur * hcur * ihprev;
-            }
-            const double pv = (i == 1) ? dia : dia - sb * cprev;
-            const double inv = 1.0 / pv;
-            dinv[i] = inv;
-            cprev = sup * inv;
-            cpr[i] = cprev;
-            hprev = hcur;
-            ihprev = ihc;
         }
     }
     __syncthreads();
     if (mine) {
         const int q = warp;  // series
-        const double *yq = b.vals + ((size_t)wm * kNSeries + q) * K;
-        double *Mq = Mv + (size_t)q * K;
+        const double *__restrict__ yq = b.vals + ((size_t)wm * kNSeries + q) * K;
+        double *__restrict__ Mq = Mv + (size_t)q * K;
         double prev = 0.0;
         double dprev = (yq[1] - yq[0]) * ih[0];
         double ylast = yq[1];
-        for (int i = 1; i <= n - 2; i++) {
-            const double ynext = yq[i + 1];
-            const double dcur = (ynext - ylast) * ih[i];
-            ylast = ynext;
-            const double rhs = 6.0 * (dcur - dprev);
-            dprev = dcur;
-            double sb = x[i] - x[i - 1];
-            if (i == n - 2) {
-                const double hb = x[n - 1] - x[n - 2];
-                sb -= hb * hb * ih[n - 3];
+        double xprev = x[0];  // x[i - 1]
+        const double hb_end = x[n - 1] - x[n - 2];
+        const double ih_end = ih[n - 3];
+        for (int i0 = 1; i0 <= n - 2; i0 += kChunk) {
+            double yn[kChunk], ihv[kChunk], dv[kChunk], xv[kChunk];
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) {
+                const int i = i0 + k;
+                const bool in = i <= n - 2;
+                yn[k] = in ? yq[i + 1] : 0.0;
+                ihv[k] = in ? ih[i] : 0.0;
+                dv[k] = in ? dinv[i] : 0.0;
+                xv[k] = in ? x[i] : 0.0;
             }
-            const double rp = (i == 1) ? rhs * dinv[1] : (rhs - sb * prev) * dinv[i];
-            Mq[i] = rp;
-            prev = rp;
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) {
+                const int i = i0 + k;
+                if (i > n - 2) break;
+                const double ynext = yn[k];
+                const double dcur = (ynext - ylast) * ihv[k];
+                ylast = ynext;
+                const double rhs = 6.0 * (dcur - dprev);
+                dprev = dcur;
+                double sb = xv[k] - xprev;
+                xprev = xv[k];
+                if (i == n - 2) sb -= hb_end * hb_end * ih_end;
+                const double rp = (i == 1) ? rhs * dv[k] : (rhs - sb * prev) * dv[k];
+                Mq[i] = rp;
+                prev = rp;
+            }
         }
         double nxt = Mq[n - 2];
-        for (int i = n - 3; i >= 1; i--) {
-            nxt = Mq[i] - cpr[i] * nxt;
-            Mq[i] = nxt;
+        for (int i0 = n - 3; i0 >= 1; i0 -= kChunk) {
+            double mv[kChunk], cv[kChunk];
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) {
+                const int i = i0 - k;
+                mv[k] = i >= 1 ? Mq[i] : 0.0;
+                cv[k] = i >= 1 ? cpr[i] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < kChunk; k++) {
+                const int i = i0 - k;
+                if (i < 1) break;
+                nxt = mv[k] - cv[k] * nxt;
+                Mq[i] = nxt;
+            }
         }
         const double h0 = x[1] - x[0], h1 = x[2] - x[1];
         const double ha = x[n - 2] - x[n - 3], hb = x[n - 1] - x[n - 2];
