@@ -547,6 +547,23 @@ def run_flow(args, world, rank, local):
     LL, like, stream, x0, prec = sampler_setup(args, rank, local)
     T, Wk = W.SAMPLER_T, W.SAMPLER_W
     xc7 = float(np.median(x0[0, :, 7]))  # reference longitude for the mode quarters
+    like_flow = None
+    if args.flow_precision == "fp64" and prec != LL.LISA_PREC_FP64:
+        # exact FP64 acceptances for the flow moves, the stretch moves in split precision
+        from paper_2005_01827_gb300 import LisaLike
+
+        like_flow = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=Wk,
+                             device=local, precision=LL.LISA_PREC_FP64, stream=stream.cuda_stream)
+        g = W.GRID_C2
+        psd = np.empty((3, g.n_bins))
+        LL.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
+        inj = np.array(W.THETA_SAMPLER_Z)
+        inj[4] = LL.lisa_dl_from_z(inj[4])
+        like_flow.set_data(g.f0, g.df, g.n_bins, None, psd)
+        h = like_flow.template(inj)
+        z = W.white_noise(g.n_bins, 2)
+        d = h + 0.5 * np.sqrt(psd / g.df) * (z[..., 0] + 1j * z[..., 1])
+        like_flow.set_data(g.f0, g.df, g.n_bins, d, psd)
     every = args.train_every
     burn = max(args.warmup, 2 * every)
     K = args.steps
@@ -558,6 +575,8 @@ def run_flow(args, world, rank, local):
         if use_flow:
             s.enable_flow(train_every=every, train_iters=400, batch=1024, lr=1e-3, seed=3,
                           freeze_after=burn)
+            if like_flow is not None:
+                s.set_flow_likelihood(like_flow)
         s.set_state(x0)
         t0 = time.perf_counter()
         s.run(burn, record=False)
@@ -600,6 +619,8 @@ def run_flow(args, world, rank, local):
     clk = clocks.stop()
     roofline, like_ms = like_roofline(LL, like, xs, prec, stream)
     like.close()
+    if like_flow is not None:
+        like_flow.close()
     p, f = out["plain"], out["flow"]
     sd = np.array(p["std"])
     sdd = np.array(p["std_dominant"])
@@ -616,7 +637,8 @@ def run_flow(args, world, rank, local):
             "n_gpus": world, "steps": K, "warmup": burn, "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == LL.LISA_PREC_SPLIT else "f64", "data": "synthetic",
-            "config": {"start": args.start, "workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
+            "config": {"start": args.start, "flow_precision": args.flow_precision,
+                       "workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
                        "(11-128-128-22, bf16 mma.sync, FP32 accumulate), trained every 500 "
                        "steps on the coldest chain until the end of burn-in, independence MH "
                        "on the coldest temperature every step",
@@ -794,6 +816,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape (8 bins per thread, groups of 8); for "
                          "profiling captures that must see one known kernel variant")
+    ap.add_argument("--flow-precision", default="same", choices=["same", "fp64"],
+                    help="flow workload: likelihood precision of the flow moves (fp64: exact "
+                         "acceptances while the stretch moves keep --precision)")
     ap.add_argument("--start", default="sky-modes", choices=["sky-modes", "true-mode"],
                     help="sampler workloads: walkers at the 8 LISA-frame sky modes (default) or "
                          "all at the injection's own sky mode")

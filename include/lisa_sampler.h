@@ -149,6 +149,12 @@ lisa_status lisa_sampler_enable_flow(lisa_sampler_t *s, const lisa_flow_schedule
 /* The sampler's flow (borrowed; NULL before lisa_sampler_enable_flow). */
 lisa_flow_t *lisa_sampler_get_flow(lisa_sampler_t *s);
 
+/* Evaluate the flow moves' proposals with another likelihood handle (borrowed, same
+ * device, same data and t0 as the sampler's, max_batch >= W), e.g. an FP64 handle for
+ * exact acceptances while the stretch moves use a split-precision one; NULL restores the
+ * sampler's own.  Requires lisa_sampler_enable_flow. */
+lisa_status lisa_sampler_set_flow_likelihood(lisa_sampler_t *s, lisa_like_t *like2);
+
 /* acc [2] = (accepted, proposed) flow moves since set_state; trainings so far; the last
  * minibatch loss of the last training (NaN before the first).  Any may be NULL. */
 lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings,

@@ -274,6 +274,7 @@ struct lisa_sampler {
     int64_t since_train = 0;     // steps recorded in the ring since the last training
     int64_t steps_run = 0;       // steps since set_state
     lisa_flowint::FStep fst{};
+    lisa_like_t *flow_like = nullptr;  // likelihood of the flow moves (default: like)
     cudaGraphExec_t gexec_flow = nullptr;
     int g_launches_flow = 0;
 };
@@ -327,8 +328,9 @@ lisa_status enqueue_step(lisa_sampler_t *s, bool with_flow, int *nl) {
         count++;
         if (s->dev.target == LISA_TARGET_LIKELIHOOD) {
             int l = 0;
-            lisa_status st = lisa::like_enqueue(s->like, s->fst.fpth, s->fst.W, s->fst.fly, s->stream, &l);
-            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->like));
+            lisa_like_t *fl = s->flow_like ? s->flow_like : s->like;
+            lisa_status st = lisa::like_enqueue(fl, s->fst.fpth, s->fst.W, s->fst.fly, s->stream, &l);
+            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(fl));
             count += l;
         }
         SCK(lisa_flowint::launch_flow_accept(s->fst, s->stream), "flow acceptance launch");
@@ -764,6 +766,26 @@ lisa_status lisa_sampler_enable_flow(lisa_sampler_t *s, const lisa_flow_schedule
 }
 
 lisa_flow_t *lisa_sampler_get_flow(lisa_sampler_t *s) { return s ? s->flow : nullptr; }
+
+lisa_status lisa_sampler_set_flow_likelihood(lisa_sampler_t *s, lisa_like_t *like2) {
+    if (!s) return LISA_ERR_ARG;
+    if (!s->flow_on) return sfail(s, LISA_ERR_STATE, "enable the flow first");
+    if (s->dev.target != LISA_TARGET_LIKELIHOOD)
+        return sfail(s, LISA_ERR_STATE, "the Gaussian target has no likelihood handle");
+    if (like2) {
+        const lisa::LikeInfo li2 = lisa::like_info(like2);
+        if (!li2.have_data) return sfail(s, LISA_ERR_STATE, "the flow's likelihood has no data");
+        if (li2.device != s->device) return sfail(s, LISA_ERR_ARG, "the flow's likelihood is on another device");
+        if (li2.max_batch < s->dev.W) return sfail(s, LISA_ERR_ARG, "the flow's likelihood needs max_batch >= n_walkers");
+        if (li2.t0 != s->li.t0) return sfail(s, LISA_ERR_ARG, "the flow's likelihood has another t0");
+        s->fst.like_err = li2.err_flag;
+    } else {
+        s->fst.like_err = s->li.err_flag;
+    }
+    s->flow_like = like2;
+    drop_graph(s);
+    return LISA_OK;
+}
 
 lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings, double *last_loss) {
     if (!s) return LISA_ERR_ARG;

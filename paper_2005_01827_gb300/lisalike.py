@@ -39,7 +39,7 @@ SYMBOLS = (
     "lisa_sampler_last_error", "lisa_sampler_to_physical", "lisa_sampler_from_physical",
     "lisa_sampler_sky_mode_init",
     "lisa_autocorr_time", "lisa_flow_default_schedule", "lisa_sampler_enable_flow",
-    "lisa_sampler_get_flow", "lisa_sampler_flow_stats",
+    "lisa_sampler_get_flow", "lisa_sampler_flow_stats", "lisa_sampler_set_flow_likelihood",
     # include/lisa_flow.h
     "lisa_flow_create", "lisa_flow_destroy", "lisa_flow_last_error", "lisa_flow_set_weights",
     "lisa_flow_get_weights", "lisa_flow_set_whitening", "lisa_flow_get_whitening",
@@ -201,6 +201,8 @@ def load(path: str = LIB_PATH):
     L.lisa_sampler_get_flow.argtypes = [vp]
     L.lisa_sampler_get_flow.restype = vp
     L.lisa_sampler_flow_stats.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
+    L.lisa_sampler_set_flow_likelihood.argtypes = [vp, vp]
+    L.lisa_sampler_set_flow_likelihood.restype = i
     L.lisa_flow_create.argtypes = [u64, C.POINTER(vp)]
     L.lisa_flow_destroy.argtypes = [vp]
     L.lisa_flow_destroy.restype = None
@@ -667,6 +669,12 @@ class LisaSampler:
         _scheck(load().lisa_sampler_enable_flow(self.h, C.byref(fs)), self.h)
         self.flow = Flow(handle=load().lisa_sampler_get_flow(self.h))
         return self.flow
+
+    def set_flow_likelihood(self, like2):
+        """Flow proposals evaluated by another LisaLike (e.g. FP64); None restores."""
+        _scheck(load().lisa_sampler_set_flow_likelihood(self.h, None if like2 is None else like2.h),
+                self.h)
+        self.flow_like = like2
 
     def flow_stats(self):
         acc = np.zeros(2, dtype=np.int64)

@@ -204,3 +204,63 @@ def test_trained_flow_sampler_mixes_faster_on_a_gaussian(pkg):
         assert np.max(np.abs(zm)) < 5.0 and np.max(np.abs(zv)) < 5.0
         taus[use_flow] = tau.max()
     assert taus[True] < 0.25 * taus[False], taus
+
+
+def test_flow_moves_with_an_fp64_likelihood_match_the_oracle(pkg, orc):
+    """A split-precision sampler whose flow moves are evaluated by an FP64 handle
+    (exact acceptances): flow-only steps on the LISA likelihood (two modes, 25,661 bins)
+    against the oracle's flow step on the oracle likelihood from the same state."""
+    LL = pkg.lisalike
+    modes, K = [(2, 2), (3, 3)], 128
+    g = W.GRID_C1
+    S = orc.psd_aet(g.freqs())
+    inj = np.array(W.THETA_C1_Z)
+    inj[4] = orc.dl_gpc(inj[4])
+    inj[10] = 1000.0
+    d = orc.template(inj, W.T0_C1, modes, K, g.f0, g.df, g.n_bins)
+    d = d + orc.noise(S, g.df, W.white_noise(g.n_bins, 6))
+    xc = orc.from_physical(inj)
+    lo, hi = W.TABLE1_LOWER, W.TABLE1_UPPER
+    Wn = 64
+    rng = np.random.default_rng(3)
+    sig = np.array([1e-4, 1e-4, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-4, 1e-4, 1e-3, 1e-4])
+    x0 = xc + sig * rng.standard_normal((Wn, D))
+    like = pkg.LisaLike(modes=modes, n_knots=K, t0=W.T0_C1, max_batch=Wn, precision=1)
+    like.set_data(g.f0, g.df, g.n_bins, d, S)
+    like64 = pkg.LisaLike(modes=modes, n_knots=K, t0=W.T0_C1, max_batch=Wn, precision=0)
+    like64.set_data(g.f0, g.df, g.n_bins, d, S)
+    s = LL.LisaSampler(like, n_temps=1, n_walkers=Wn, seed=13, lisa_frame=0, lower=lo, upper=hi)
+    fl = s.enable_flow(train_every=0, flow_only=1)
+    s.set_flow_likelihood(like64)
+    w = W.flow_init_weights(4, out_scale=0.05)
+    mu_q, L_q = xc, np.diag(1.5 * sig)
+    fl.set_weights(w)
+    fl.set_whitening(mu_q, L_q)
+    s.set_state(x0[None])
+
+    def target(y):
+        th = np.array([orc.to_physical(v, False, W.T0_C1) for v in y])
+        return orc.loglike(th, W.T0_C1, modes, K, g.f0, g.df, d, S)[0]
+
+    snr2 = orc.inner(d, d, S, g.df)
+    n_acc = n_bad = 0
+    for _ in range(3):
+        x, lnl, _, st = s.state()
+        lnl_o = target(x[0])                          # the state's ln L on the oracle
+        s.run(1)
+        x2, lnl2, _, _ = s.state()
+        xo, lo_, _, acc, lr = F.flow_mh_step(w, mu_q, L_q, x[0], lnl_o, np.zeros(Wn), 1.0, 13,
+                                             st, lo, hi, target)
+        gacc = ~np.all(x2[0] == x[0], axis=1)
+        u = F.accept_units(13, st, range(Wn))
+        bad = gacc != acc
+        assert np.all(np.abs(np.log(u[bad]) - lr[bad]) < 1e-3)
+        n_bad += bad.sum()
+        n_acc += gacc.sum()
+        both = gacc & acc
+        # accepted walkers carry the FP64 ln L of their new position
+        assert np.max(np.abs(lnl2[0][both] - lo_[both]), initial=0.0) <= 1e-6 * snr2
+    s.close()
+    like.close()
+    like64.close()
+    assert n_acc > 0 and n_bad <= 2
