@@ -76,8 +76,8 @@ def fp32_peak_tflops():
 
 def fp64_peak_tflops():
     """FP64 pipe peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per
-    clock per SM x 2 flops x 2.07 GHz (the unit count measured by an FMA-chain probe:
-    1.19 TFLOP/s at the running clock)."""
+    clock per SM x 2 flops x 2.07 GHz.  The bench line also carries the rate that
+    lisa_probe_pipes measures on the device at its running clock."""
     return 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -312,6 +312,7 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     tpw = TRAFFIC_SPLIT_PER_WALKER_BIN.get(tuple(shape[:2]))
+    probe = lisalike.probe_pipes(torch.cuda.current_device())
     return {"value": job_value(world, B, args.steps, ms), "unit": "evals/s",
             "ms_per_step": ms / args.steps, "dtype": "f32+f64", "graphs": graphs,
             "tile": {"bins_per_thread": shape[0], "group": shape[1], "blocks": shape[2]},
@@ -328,6 +329,11 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
                                      "(the phasor is a table and polynomials); ncu: issue 63 %, "
                                      "FMA pipe 43 %, ALU 28 %"},
                          "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
+                         "measured_pipes": {
+                             "fp32_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
+                             "frac_of_measured_fp32":
+                                 achieved / (2 * probe["fp32_fma_per_s"] / 1e12),
+                             "source": "lisa_probe_pipes: FMA chains on every SM"},
                          "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
                                                zip(("knots", "splines", "segprep", "plan",
                                                     "dense", "finish"), stage_ms)}}}
@@ -923,6 +929,7 @@ def main():
     peak = fp64_peak_tflops()
     tpw = TRAFFIC_F64_PER_WALKER_BIN.get(tuple(shape[:2]))
     traffic = tpw * bins if tpw else None
+    probe = lisalike.probe_pipes(local)      # measured pipe rates of this device
     roofline = {"bound": "alu", "kernel": "dense_f64_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
@@ -932,7 +939,12 @@ def main():
                                       zip(("knots", "splines", "segprep", "plan", "dense",
                                            "finish"), stage_ms)},
                 "hbm_gbs": BYTES_BIN * bins / (dense_ms * 1e-3) / 1e9,
-                "hbm_peak_gbs": peaks().get("hbm_gbs")}
+                "hbm_peak_gbs": peaks().get("hbm_gbs"),
+                "measured_pipes": {"fp64_tflops": 2 * probe["fp64_fma_per_s"] / 1e12,
+                                   "fp32_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
+                                   "mufu_gops": probe["mufu_per_s"] / 1e9,
+                                   "frac_of_measured_fp64": achieved / (2 * probe["fp64_fma_per_s"] / 1e12),
+                                   "source": "lisa_probe_pipes: FMA / MUFU chains on every SM"}}
     hbm_peak = peaks().get("hbm_gbs")
     roofline["fractions"] = {
         "binding": "fp64", "fp64": achieved / peak, "fp32": 0.0, "mufu": 0.0,

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liblisalike.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 SOURCES = ["lisa_like.cu", "stages.cu", "plan.cu", "dense.cu", "split.cu", "noalloc.cu",
-           "sampler.cu", "flow.cu", "rb.cu"]
+           "sampler.cu", "flow.cu", "rb.cu", "probe.cu"]
 
 
 def nvcc() -> str:

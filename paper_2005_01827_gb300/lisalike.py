@@ -40,6 +40,8 @@ SYMBOLS = (
     "lisa_sampler_sky_mode_init",
     "lisa_autocorr_time", "lisa_flow_default_schedule", "lisa_sampler_enable_flow",
     "lisa_sampler_get_flow", "lisa_sampler_flow_stats", "lisa_sampler_set_flow_likelihood",
+    # include/lisa_probe.h
+    "lisa_probe_pipes",
     # include/lisa_flow.h
     "lisa_flow_create", "lisa_flow_destroy", "lisa_flow_last_error", "lisa_flow_set_weights",
     "lisa_flow_get_weights", "lisa_flow_set_whitening", "lisa_flow_get_whitening",
@@ -194,6 +196,8 @@ def load(path: str = LIB_PATH):
     L.lisa_sampler_from_physical.argtypes = [vp, i, i, d, vp]
     L.lisa_sampler_sky_mode_init.argtypes = [vp, vp, vp, vp, i, i, u64, vp]
     L.lisa_autocorr_time.argtypes = [vp, i, i, i, i, dp, vp, vp]
+    L.lisa_probe_pipes.argtypes = [i, dp]
+    L.lisa_probe_pipes.restype = i
     fsp = C.POINTER(lisa_flow_schedule)
     L.lisa_flow_default_schedule.argtypes = [fsp]
     L.lisa_flow_default_schedule.restype = None
@@ -852,3 +856,11 @@ class Flow:
                                        float(lr), int(seed), int(round_), _ptr(loss), None),
                 self.h)
         return loss
+
+
+def probe_pipes(device=0):
+    """Measured FP64 FMA/s, FP32 FMA/s, MUFU sin/s of the device and its SM clock [Hz]."""
+    out = (C.c_double * 4)()
+    _check(load().lisa_probe_pipes(int(device), out))
+    return {"fp64_fma_per_s": out[0], "fp32_fma_per_s": out[1], "mufu_per_s": out[2],
+            "sm_clock_hz": out[3]}
