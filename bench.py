@@ -204,7 +204,7 @@ def work_units(like, th):
     return mode_bins, bins
 
 
-def cpu_baseline(sample_walkers=16, threads=None):
+def cpu_baseline(sample_walkers=192, threads=None):
     """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
     import oracle
 
@@ -347,7 +347,7 @@ SAMPLER_WORKLOAD = ("parallel-tempered stretch-move sampler, 8 temperatures x 25
                     "Msun, q=0.5, z=3 (SNR ~880) + seeded noise")
 
 
-def sampler_cpu_baseline(steps=4):
+def sampler_cpu_baseline(steps=16):
     """The oracle sampler as it stands on a bounded sample: 2 temperatures x 8 walkers of
     the same workload for a few steps (each step = 16 oracle ln L evaluations)."""
     import oracle
