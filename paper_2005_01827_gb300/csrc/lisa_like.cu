@@ -47,7 +47,7 @@ struct lisa_like {
     double f0 = 0.0, df = 0.0, dd = 0.0;
     int N = 0;
     double *bins = nullptr;   // [N][9] FP64 staged data
-    float *bins32 = nullptr;  // [N][9] FP32 whitened data (split precision)
+    float *bins32 = nullptr;  // [N][kBinFloats] FP32 whitened data (split precision)
     SegRec *segs = nullptr;   // [max_batch][L][K-1] split-precision segment records
     unsigned long long *phases = nullptr;  // [max_batch][L][K-1][8] FP64-path phase records
 

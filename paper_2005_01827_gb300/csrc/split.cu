@@ -9,6 +9,10 @@
 // exact modular integer additions, so no rounding accumulates along a segment; its top
 // 8 bits index a table of e^{2 pi i k / 256} and the next 23 bits give a small angle
 // (< 2 pi / 256) whose sine and cosine are short FP32 polynomials.
+//
+// Packed FP32: each channel's (Re, Im) transfer pair is one Horner evaluation in
+// Blackwell's f32x2 FMA (one instruction for both lanes, each rounded as the scalar
+// FMA), and the per-bin integrand runs on (re, im) pairs the same way.
 #include "kernels.h"
 #include "model.cuh"
 #include "split.h"
@@ -46,7 +50,8 @@ __device__ __forceinline__ double bin_freq_s(double f0, double df, int j) {
 }
 
 // ------------------------------------------------------------------------ data prep
-// Whitened FP32 data: s = sqrt(w) 2^-64 and d_hat = sqrt(w) d per channel, w = 4 df / S.
+// Whitened FP32 data: s = sqrt(w) 2^-64 and -2 d_hat = -2 sqrt(w) d per channel,
+// w = 4 df / S.
 __global__ void __launch_bounds__(256) prep_split_kernel(const double *__restrict__ bins, int N,
                                                          float *__restrict__ out) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
@@ -57,8 +62,8 @@ __global__ void __launch_bounds__(256) prep_split_kernel(const double *__restric
             const double sw = sqrt(w);
             o[c] = (float)(sw * 5.421010862427522e-20);
             // (w d) / sqrt(w) = sqrt(w) d
-            o[3 + 2 * c] = (float)(b[3 + 2 * c] / sw);
-            o[4 + 2 * c] = (float)(b[4 + 2 * c] / sw);
+            o[3 + 2 * c] = (float)(-2.0 * b[3 + 2 * c] / sw);
+            o[4 + 2 * c] = (float)(-2.0 * b[4 + 2 * c] / sw);
         }
     }
 }
@@ -116,11 +121,14 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
                 r.ph[7] = 0;
                 continue;
             }
+            // A at c[0..3]; Re and Im of each channel's transfer interleaved after it
             const double sc = (q == 0) ? kAmpScale : 1.0;
-            r.c[4 * slot + 0] = (float)(sc * y);
-            r.c[4 * slot + 1] = (float)(sc * y1 * wd);
-            r.c[4 * slot + 2] = (float)(sc * y2 * wd * wd);
-            r.c[4 * slot + 3] = (float)(sc * c3 * wd * wd * wd);
+            const int base = slot == 0 ? 0 : 4 + 8 * ((slot - 1) >> 1) + ((slot - 1) & 1);
+            const int step = slot == 0 ? 1 : 2;
+            r.c[base] = (float)(sc * y);
+            r.c[base + step] = (float)(sc * y1 * wd);
+            r.c[base + 2 * step] = (float)(sc * y2 * wd * wd);
+            r.c[base + 3 * step] = (float)(sc * c3 * wd * wd * wd);
             slot++;
         }
         if (kFull) {
@@ -167,6 +175,41 @@ __device__ __forceinline__ int seg_guess(const int *__restrict__ kb, int K, int 
     while (s < K - 2 && __ldg(kb + s + 1) <= j) s++;
     return s;
 }
+
+// packed FP32 pairs (Blackwell f32x2): one instruction, each lane rounded as its scalar
+// counterpart
+#define LISA_F32X2(op, ...)                                                                  \
+    asm("{\n.reg .b64 ra, rb, rc, rd;\n"                                                      \
+        "mov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n" op         \
+        "\nmov.b64 {%0, %1}, rd;\n}"                                                          \
+        : "=f"(d.x), "=f"(d.y)                                                              \
+        : __VA_ARGS__)
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    LISA_F32X2("fma.rn.f32x2 rd, ra, rb, rc;", "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x),
+               "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    LISA_F32X2("mul.rn.f32x2 rd, ra, rb;", "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(0.0f),
+               "f"(0.0f));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    LISA_F32X2("add.rn.f32x2 rd, ra, rb;", "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(0.0f),
+               "f"(0.0f));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    LISA_F32X2("sub.rn.f32x2 rd, ra, rb;", "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(0.0f),
+               "f"(0.0f));
+    return d;
+}
+#undef LISA_F32X2
 
 struct PhaseState {
     unsigned long long ph, d1, d2, d3;
@@ -264,6 +307,36 @@ __device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
         two_sum(hi, h2, s, e);
         hi = s;
         lo = lo + l2 + e;
+    }
+}
+
+// the seven FP32 series of a record at in-segment coordinate tt = (t, t): the amplitude
+// by scalar Horner, each channel's (Re, Im) transfer pair by packed Horner
+__device__ __forceinline__ void eval_series(const SegCoef &r, float2 tt, float &amp,
+                                            float2 tr[3]) {
+    const float t = tt.x;
+    amp = fmaf(t, fmaf(t, fmaf(t, r.c[3], r.c[2]), r.c[1]), r.c[0]);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float *k = r.c + 4 + 8 * c;
+        float2 x = fma2(tt, make_float2(k[6], k[7]), make_float2(k[4], k[5]));
+        x = fma2(tt, x, make_float2(k[2], k[3]));
+        tr[c] = fma2(tt, x, make_float2(k[0], k[1]));
+    }
+}
+
+// h += T A e^{i phi} for the three channels of one bin
+__device__ __forceinline__ void add_mode(const PhaseState &p, const float2 *__restrict__ tab,
+                                         float amp, const float2 tr[3], float hr[3],
+                                         float hm[3]) {
+    float zr, zi;
+    phasor(p.ph, tab, zr, zi);
+    zr *= amp;
+    zi *= amp;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        hr[c] = fmaf(tr[c].x, zr, fmaf(-tr[c].y, zi, hr[c]));
+        hm[c] = fmaf(tr[c].x, zi, fmaf(tr[c].y, zr, hm[c]));
     }
 }
 
@@ -372,31 +445,20 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 SegCoef r = seg_coef(sg + s);
                 int knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
                 PhaseState p = phase_at(sg + s, ja - r.kb0);
-                float t = (float)(ja - r.kb0) * r.invw;
+                const float ta = (float)(ja - r.kb0) * r.invw;
+                float2 tt = make_float2(ta, ta);  // (t, t): the packed Horner operand
                 if (ja == j0 && jb == j0 + C && knext >= j0 + C) {
                     // the whole chunk lies in one segment and in the band: no predicates
 #pragma unroll
                     for (int i = 0; i < C; i++) {
-                        float v[7];
-#pragma unroll
-                        for (int q = 0; q < 7; q++)
-                            v[q] = fmaf(t, fmaf(t, fmaf(t, r.c[4 * q + 3], r.c[4 * q + 2]),
-                                                r.c[4 * q + 1]),
-                                        r.c[4 * q]);
-                        float zr, zi;
-                        phasor(p.ph, tab, zr, zi);
-                        zr *= v[0];
-                        zi *= v[0];
-#pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            const float tr = v[1 + 2 * c], ti = v[2 + 2 * c];
-                            hr[i][c] = fmaf(tr, zr, fmaf(-ti, zi, hr[i][c]));
-                            hm[i][c] = fmaf(tr, zi, fmaf(ti, zr, hm[i][c]));
-                        }
+                        float amp;
+                        float2 tr[3];
+                        eval_series(r, tt, amp, tr);
+                        add_mode(p, tab, amp, tr, hr[i], hm[i]);
                         p.ph += p.d1;
                         p.d1 += p.d2;
                         p.d2 += p.d3;
-                        t += r.invw;
+                        tt = add2(tt, make_float2(r.invw, r.invw));
                     }
                     continue;
                 }
@@ -409,59 +471,45 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                         r = seg_coef(sg + s);
                         knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
                         p = phase_at(sg + s, j - r.kb0);
-                        t = (float)(j - r.kb0) * r.invw;
+                        const float tj = (float)(j - r.kb0) * r.invw;
+                        tt = make_float2(tj, tj);
                     }
-                    float v[7];
-#pragma unroll
-                    for (int q = 0; q < 7; q++)
-                        v[q] = fmaf(t, fmaf(t, fmaf(t, r.c[4 * q + 3], r.c[4 * q + 2]),
-                                            r.c[4 * q + 1]),
-                                    r.c[4 * q]);
-                    float zr, zi;
-                    phasor(p.ph, tab, zr, zi);
-                    zr *= v[0];
-                    zi *= v[0];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float tr = v[1 + 2 * c], ti = v[2 + 2 * c];
-                        hr[i][c] = fmaf(tr, zr, fmaf(-ti, zi, hr[i][c]));
-                        hm[i][c] = fmaf(tr, zi, fmaf(ti, zr, hm[i][c]));
-                    }
+                    float amp;
+                    float2 tr[3];
+                    eval_series(r, tt, amp, tr);
+                    add_mode(p, tab, amp, tr, hr[i], hm[i]);
                     p.ph += p.d1;
                     p.d1 += p.d2;
                     p.d2 += p.d3;
-                    t += r.invw;
+                    tt = add2(tt, make_float2(r.invw, r.invw));
                 }
             }
 
-            // per-bin integrand |h|^2 - 2 Re(d h*) and |h|^2 in whitened units, compensated
-            float rs = 0.0f, rc = 0.0f, hs = 0.0f, hc = 0.0f;
+            // per-bin integrand |h|^2 - 2 Re(d h*) and |h|^2 in whitened units, packed as
+            // (re, im) pairs per channel, then compensated (Kahan) sums over the chunk of
+            // the pair (integrand, |h|^2)
+            float2 sum = make_float2(0.0f, 0.0f), comp = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int i = 0; i < C; i++) {
                 const int j = j0 + i;
                 if (j >= Jend) continue;
                 const float *o = sbin + (j - J0) * kBinFloats;
-                float ri = 0.0f, hi2 = 0.0f;
+                float2 ri = make_float2(0.0f, 0.0f), hh = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     const float sw = o[c];
-                    const float xr = sw * hr[i][c], xi = sw * hm[i][c];
-                    const float er = fmaf(-2.0f, o[3 + 2 * c], xr);
-                    const float ei = fmaf(-2.0f, o[4 + 2 * c], xi);
-                    ri = fmaf(xr, er, fmaf(xi, ei, ri));
-                    hi2 = fmaf(xr, xr, fmaf(xi, xi, hi2));
+                    const float2 x = mul2(make_float2(sw, sw), make_float2(hr[i][c], hm[i][c]));
+                    const float2 e = add2(x, make_float2(o[3 + 2 * c], o[4 + 2 * c]));
+                    ri = fma2(x, e, ri);
+                    hh = fma2(x, x, hh);
                 }
-                float y = ri - rc;
-                float tt = rs + y;
-                rc = (tt - rs) - y;
-                rs = tt;
-                y = hi2 - hc;
-                tt = hs + y;
-                hc = (tt - hs) - y;
-                hs = tt;
+                const float2 y = sub2(make_float2(ri.x + ri.y, hh.x + hh.y), comp);
+                const float2 t2 = add2(sum, y);
+                comp = sub2(sub2(t2, sum), y);
+                sum = t2;
             }
             // FP32 (value, compensation) pairs summed across the warp; FP64 from here up
-            float rl = -rc, hl = -hc;
+            float rs = sum.x, hs = sum.y, rl = -comp.x, hl = -comp.y;
             warp_sum_pair(rs, rl);
             warp_sum_pair(hs, hl);
             if ((tid & 31) == 0) red[k][tid >> 5] = make_float4(rs, rl, hs, hl);

@@ -6,14 +6,17 @@
 
 namespace lisa {
 
-// FP32 staged data per bin: s_A, s_E, s_T (sqrt(w) 2^-64), then sqrt(w) d for A, E, T
-// (re, im); 36 bytes.
+// FP32 staged data per bin: s_A, s_E, s_T (s_X = sqrt(w_X) 2^-64), then -2 sqrt(w_X) d_X
+// for X = A, E, T (re, im); 36 bytes, so that a tile of 1024 bins takes 36 KB of shared
+// memory and four blocks per SM leave L1 room for the segment records.
 constexpr int kBinFloats = 9;
 
-// One spline segment of one (walker, mode) in the split-precision form, 192 bytes:
-// c[4 q + k] is the t^k coefficient (t = (j - kb0) / W over the segment's W bins) of
-// series q = A 2^64, Re T^A, Im T^A, Re T^E, Im T^E, Re T^T, Im T^T; ph[] is the
-// fixed-point phase record of the segment (see kernels.h).
+// One spline segment of one (walker, mode) in the split-precision form, 192 bytes.
+// With t = (j - kb0) / W over the segment's W bins: c[k] is the t^k coefficient of
+// A 2^64, and for channel x = 0, 1, 2 (A, E, T) c[4 + 8 x + 2 k] and c[4 + 8 x + 2 k + 1]
+// are the t^k coefficients of Re T^X and Im T^X, interleaved so that the pair is one
+// packed f32x2 operand.  ph[] is the fixed-point phase record of the segment (see
+// kernels.h).
 struct __align__(16) SegRec {
     float c[28];
     unsigned long long ph[kPhaseWords];
