@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 comp = sub2(sub2(t2, sum), y);
                 sum = t2;
             }
-            // FP32 (value, compensation) pairs summed across the warp; FP64 from here up
+            // FP32 (value, compensation) pairs summed error-free across the warp here and
+            // across the block below; FP64 from the block's partial up
             float rs = sum.x, hs = sum.y, rl = -comp.x, hl = -comp.y;
             warp_sum_pair(rs, rl);
             warp_sum_pair(hs, hl);
