@@ -64,6 +64,8 @@ struct Source {
     double xrd;      // remnant ringdown frequency in M f
     double phj, c1, c2;  // merger-ringdown continuation: phj + c1 (x - xj) - c2 (1/x - 1/xj)
     double xpk, phpk, dphpk;  // peak of f^2 A_22, the raw phase and slope there
+    double k128;     // 1 / (128 eta), the leading phase coefficient
+    double m2pi;     // M / (2 pi)
 };
 
 // Inspiral phase and its first two x-derivatives at x = M f (t_c = 0 frame).
@@ -125,6 +127,8 @@ __device__ inline bool make_source_core(const double *th, double t0, Source &s) 
     s.psi = th[9];
     s.tc = th[10] + t0;
     const double eta = s.eta;
+    s.k128 = 1.0 / (128.0 * eta);
+    s.m2pi = s.M / kTwoPi;
     s.amp0 = sqrt(2.0 * eta / 3.0) * pow(kPi, -1.0 / 6.0) * s.M * s.M / s.dist;
     s.al2 = -323.0 / 224.0 + 451.0 / 168.0 * eta;
     s.al3 = (27.0 / 8.0 - 11.0 / 6.0 * eta) * s.chis + 27.0 / 8.0 * s.dlt * s.chia;
@@ -208,7 +212,12 @@ __device__ inline double amp_ratio(const Source &s, const Mode &md, double v) {
     if (id == 3) r = sqrt(2.0) / 3.0 * s.dlt * v;
     if (id == 4) r = 1.0 / 3.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * s.eta) * v * v;
     if (id == 5) r = 9.0 / (4.0 * sqrt(70.0)) * s.dlt * (1.0 - 2.0 * s.eta) * v * v * v;
-    return r * sqrt(2.0 / md.m);
+    // sqrt(2 / m) for m = 1..4
+    const double sq = md.m == 1   ? 1.4142135623730951
+                      : md.m == 2 ? 1.0
+                      : md.m == 3 ? 0.816496580927726
+                                  : 0.7071067811865476;
+    return r * sq;
 }
 
 __device__ inline double phase_offset(const Mode &md) {
@@ -250,20 +259,20 @@ __device__ inline void mode_all(const Source &s, const Mode &md, double f, doubl
     if (x <= kXJoin) {
         const double iv = 1.0 / v;
         const double iv2 = iv * iv, iv3 = iv2 * iv, iv5 = iv3 * iv2;
-        const double k = 1.0 / (128.0 * s.eta);
+        const double k = s.k128;
         p = -3.0 * k * (iv5 + s.ps2 * iv3 + s.ps3 * iv2);
         dp = k * ix * (5.0 * iv5 + 3.0 * s.ps2 * iv3 + 2.0 * s.ps3 * iv2);
     } else {
         p = s.phj + s.c1 * (x - kXJoin) - s.c2 * (ix - 1.0 / kXJoin);
         dp = s.c1 + s.c2 * ix * ix;
     }
-    time = s.tc - s.M / kTwoPi * (dp - s.dphpk);
+    time = s.tc - s.m2pi * (dp - s.dphpk);
     phase = 0.5 * md.m * (p - s.phpk - s.dphpk * (x - s.xpk)) + phase_offset(md);
     const double r = x / s.xrd;
     const double r2 = r * r;
     const double x16 = sqrt(v * 0.68278406325529568);  // x^(1/6); 0.6827... = pi^(-1/3)
-    const double a22 = s.amp0 * ix / x16 * exp(s.al2 * v * v + s.al3 * v * v * v) /
-                       (1.0 + r2 * r2 * r2);
+    const double a22 = s.amp0 * ix * exp(s.al2 * v * v + s.al3 * v * v * v) /
+                       (x16 * (1.0 + r2 * r2 * r2));
     amp = amp_ratio(s, md, v) * a22;
 }
 
@@ -364,7 +373,9 @@ __device__ inline double delay_phase(const Frame &fr, double f, double t) {
 
 // TDI A, E, T transfer of one mode at (f, t), Eqs. (7)-(10).  The two directions of an
 // arm share n n^T (so the polarisation factor) and the propagation phase; only the
-// sinc argument differs.
+// sinc argument differs.  The constellation of constellation() is rigid: every arm
+// q_c - q_a has length L exactly (to rounding), so the unit vector is (q_c - q_a) / L;
+// the two sinc quotients of an arm share one division.
 __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f, double t,
                                     cplx out[3], double *delay) {
     double p0[3], q[3][3];
@@ -378,13 +389,9 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
     for (int e = 0; e < 3; e++) {
         const int a = pa[e], c = pb[e];
         double n[3];
-        double nn = 0.0;
+        const double inv = 1.0 / L;
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            n[i] = q[c][i] - q[a][i];
-            nn += n[i] * n[i];
-        }
-        const double inv = 1.0 / sqrt(nn);
+        for (int i = 0; i < 3; i++) n[i] = q[c][i] - q[a][i];
         double kn = 0.0, kq = 0.0, xp = 0.0, xc = 0.0;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -406,8 +413,16 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
         const cplx F = {kp.re * xp + kc.re * xc, kp.im * xp + kc.im * xc};
         const cplx eF = cmul(cexpi(-kPi * f * (L + kq)), F);
         const double a1 = pfl * (1.0 - kn), a2 = pfl * (1.0 + kn);  // a -> c and c -> a
-        const double s1 = (a1 == 0.0) ? 1.0 : sin(a1) / a1;
-        const double s2 = (a2 == 0.0) ? 1.0 : sin(a2) / a2;
+        double s1, s2;
+        const double a12 = a1 * a2;
+        if (a12 != 0.0) {
+            const double r = 1.0 / a12;
+            s1 = sin(a1) * (a2 * r);
+            s2 = sin(a2) * (a1 * r);
+        } else {
+            s1 = (a1 == 0.0) ? 1.0 : sin(a1) / a1;
+            s2 = (a2 == 0.0) ? 1.0 : sin(a2) / a2;
+        }
         // -i pfl sinc e F
         y[a][c] = {pfl * s1 * eF.im, -pfl * s1 * eF.re};
         y[c][a] = {pfl * s2 * eF.im, -pfl * s2 * eF.re};
