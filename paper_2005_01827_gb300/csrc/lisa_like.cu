@@ -340,7 +340,7 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     LCK(launch_finish(d, b, h->tune.group, split ? 1 : 0, h->dd, lnL, dh, hh, s),
         "finish kernel launch");
     LCK(mark(6), "cudaEventRecord");
-    h->last_launches = 7;  // band + knot kernels, splines, segments, plan, dense, finish
+    h->last_launches = 8;  // band, knots, spline solve + coefficients, segments, plan, dense, finish
     return LISA_OK;
 }
 

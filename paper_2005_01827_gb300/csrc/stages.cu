@@ -97,14 +97,16 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
     const int K = d.K;
     const double flo = b.fedge[(size_t)wm * 2], fhi = b.fedge[(size_t)wm * 2 + 1];
     const double r = log(fhi / flo);
+    const double idf = 1.0 / d.df;
     double *fkm = b.fk + (size_t)wm * K;
     int *kbm = b.kb + (size_t)wm * K;
     double *vm = b.vals + (size_t)wm * kNSeries * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const double f = (k == K - 1) ? fhi : flo * exp(r * (double)k / (double)(K - 1));
         fkm[k] = f;
-        // first dense bin at or above this knot
-        double g = ceil((f - d.f0) / d.df);
+        // first dense bin at or above this knot: a guess from 1/df, then exact by the
+        // bin frequencies themselves
+        double g = ceil((f - d.f0) * idf);
         int j = g <= 0.0 ? 0 : (g >= (double)d.N ? d.N : (int)g);
         while (j > 0 && bin_freq(d.f0, d.df, j - 1) >= f) j--;
         while (j < d.N && bin_freq(d.f0, d.df, j) < f) j++;
@@ -144,9 +146,9 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 // 8 series of one (walker, mode) share the matrix.  A block owns 32 systems and every
 // lane one system, so the serial recurrences keep all 32 lanes busy (GB300's FP64 pipe
 // spends a full warp's time on every FP64 instruction whatever the active mask): warp 0
-// factorises the 32 matrices, warp q sweeps series q of the 32 systems, then all
-// threads emit the per-segment coefficients.  The factorisation lives in global
-// scratch rows next to the second derivatives.
+// factorises the 32 matrices, warp q sweeps series q of the 32 systems; a second,
+// grid-stride kernel emits the per-segment coefficients.  The factorisation lives in
+// global scratch rows next to the second derivatives.
 constexpr int kSplineSystems = 32;
 
 // The three serial recurrences (factorisation, forward and backward sweeps) load their
@@ -266,13 +268,20 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
         Mq[0] = ((h0 + h1) * Mq[1] - h0 * Mq[2]) * ih[1];
         Mq[n - 1] = ((ha + hb) * Mq[n - 2] - hb * Mq[n - 3]) * ih[n - 3];
     }
-    __syncthreads();
-    // coefficients: per segment and series of the block's systems
-    const int per_sys = (n - 1) * kNSeries;
-    for (int t = threadIdx.x; t < kSplineSystems * per_sys; t += blockDim.x) {
-        const int sys = t / per_sys, rem = t % per_sys;
-        const int w2 = blockIdx.x * kSplineSystems + sys;
-        if (w2 >= nsys || !b.band[(size_t)w2 * 3]) continue;
+}
+
+// Cubic coefficients of every (system, segment, series) from the second derivatives, as
+// a grid-stride kernel of its own: the blocks of the solve do not divide evenly over the
+// SMs, this FP64 work does.
+__global__ void __launch_bounds__(256) spline_coef_kernel(StageDims d, StageBufs b) {
+    const int K = d.K;
+    const long long per_sys = (long long)(K - 1) * kNSeries;
+    const long long total = (long long)d.B * d.L * per_sys;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long w2 = t / per_sys;
+        const int rem = (int)(t - w2 * per_sys);
+        if (!b.band[w2 * 3]) continue;
         const int sgm = rem / kNSeries, q = rem % kNSeries;
         const double *x2 = b.fk + (size_t)w2 * K;
         const double *M2 = b.mscratch + (size_t)w2 * kScratchRows * K;
@@ -291,6 +300,12 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
     const int nsys = d.B * d.L;
     spline_kernel<<<(nsys + kSplineSystems - 1) / kSplineSystems, 256, 0, s>>>(d, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)nsys * (d.K - 1) * kNSeries;
+    const long long want = (total + 255) / 256, cap = 152LL * 8;  // 8 blocks per SM
+    const int blocks = (int)(want < cap ? want : cap);
+    spline_coef_kernel<<<blocks, 256, 0, s>>>(d, b);
     return cudaGetLastError();
 }
 

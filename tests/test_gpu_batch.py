@@ -47,7 +47,7 @@ def test_graph_replay_equals_direct_calls(pkg, orc):
             LL.lisa_like_loglike_device(like.h, dp, 40, out, None, None, st.cuda_stream)
             st.synchronize()
             assert np.array_equal(out.cpu().numpy(), ref)
-        assert like.last_launches() == 7
+        assert like.last_launches() == 8
         like.close()
 
 
