@@ -40,11 +40,12 @@ WORKLOAD_C3 = ("8192 walkers with M_T log-uniform in [1e3, 1e9] Msun, 6 modes, K
                "1-yr grid (3155445 bins), A/E/T, FP64, CUDA-graph replay, autotuned tiles, "
                "Binary-1 injection + seeded noise")
 # algorithmic work (see the design notes): per (walker, mode, active bin) 8 cubic Horner
-# evaluations (48), the segment offset (1), the t_coal ramp (2), e^{i phi} (20: a table
-# entry rotated by sine and cosine polynomials of the remaining angle), A e^{i phi} (2),
-# three complex transfer products accumulated into the mode sum (24) = 97 flops; per
+# evaluations (48), the segment offset (1), the t_coal ramp (2), e^{i phi} (18: a table
+# entry rotated by sine and cosine polynomials of the remaining angle, r = (x - 1) step as
+# one FMA, sine to r^5, cosine to r^4 with a fitted r^4 coefficient), A e^{i phi} (2),
+# three complex transfer products accumulated into the mode sum (24) = 95 flops; per
 # (walker, bin) f_j (2) and the three-channel integrand (27) = 29 flops.
-FLOP_MODE_BIN = 48 + 1 + 2 + 20 + 2 + 24
+FLOP_MODE_BIN = 48 + 1 + 2 + 18 + 2 + 24
 FLOP_BIN = 29
 # data bytes streamed per bin by a walker tile (w and w*d for A, E, T, FP64) and the
 # spline coefficients per segment (8 series x 4 doubles)
@@ -53,8 +54,8 @@ BYTES_BIN = 72
 # (dram__bytes_read.sum + dram__bytes_write.sum over 69,589,136 walker-bins), per tile
 # shape (bins per thread, group); scaled to a launch by its walker-bins.  A shape without
 # a capture reports null.
-TRAFFIC_F64_PER_WALKER_BIN = {(8, 8): (753.95e6 + 4.90e6) / 69589136,
-                              (4, 8): (754.31e6 + 6.07e6) / 69589136}
+TRAFFIC_F64_PER_WALKER_BIN = {(8, 8): (753.79e6 + 5.11e6) / 69589136,
+                              (4, 8): (755.36e6 + 6.43e6) / 69589136}
 TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (375.16e6 + 4.56e6) / 69589136}
 
 
@@ -950,8 +951,9 @@ def main():
     roofline["fractions"] = {
         "binding": "fp64", "fp64": achieved / peak, "fp32": 0.0, "mufu": 0.0,
         "hbm": (traffic / (dense_ms * 1e-3) / 1e9 / hbm_peak) if (traffic and hbm_peak) else None,
-        "note": "fp32 and mufu: the FP64 kernel's inner loop issues neither (ncu: FMA pipe "
-                "0.7 %, XU ~0 %); hbm: measured DRAM bytes per launch over the launch time"}
+        "note": "fp32 and mufu: the FP64 kernel's inner loop issues neither (ncu <4,8>: FP64 "
+                "pipe 94 % busy, FMA pipe 1.0 %); hbm: measured DRAM bytes per launch over "
+                "the launch time"}
     if c3:
         roofline["note"] = "stage times from one profiled call before graph replay"
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,

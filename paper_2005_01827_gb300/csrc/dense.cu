@@ -78,16 +78,23 @@ __device__ __forceinline__ Phase64 phase64_at(const unsigned long long *__restri
 }
 
 // e^{2 pi i ph / 2^64} in FP64: the top 10 bits select e^{2 pi i k / 1024}, the next 52
-// bits give r < 2 pi / 1024, and sin r, cos r are Taylor polynomials whose truncation
-// error is below 1e-17
+// bits give r < 2 pi / 1024 = R, sin r is its Taylor polynomial to r^5 (truncation below
+// 1e-19) and cos r = 1 - s/2 + c s^2 with s = r^2: the s^3 term of the Taylor series is
+// absorbed into c, chosen so that the error c s^2 - (1/24 - s/720 + ...) s^2 equioscillates
+// over s in [0, R^2] (c = 1/24 - k R^2 with 76800 k^3 + k = 1/720; truncation below 8e-18)
+constexpr double kStep64 = 6.1359231515425647e-03;  // 2 pi / 1024
+constexpr double kCos2 = 0.041666619912852754;
+
 __device__ __forceinline__ void phasor64(unsigned long long ph, const double2 *__restrict__ tab,
                                          double &zr, double &zi) {
     const double2 t = tab[ph >> 54];
-    const double u = __longlong_as_double(0x3ff0000000000000ull | ((ph << 10) >> 12)) - 1.0;
-    const double r = u * 6.1359231515425647e-03;  // 2 pi / 1024
+    // x in [1, 2) carries the next 52 bits; fma(x, step, -step) = (x - 1) step exactly
+    // rounded once, as (x - 1) is exact
+    const double x = __longlong_as_double(0x3ff0000000000000ull | ((ph << 10) >> 12));
+    const double r = fma(x, kStep64, -kStep64);
     const double r2 = r * r;
     const double sn = r * fma(r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
-    const double cs = fma(r2, fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double cs = fma(r2, fma(r2, kCos2, -0.5), 1.0);
     zr = fma(t.x, cs, -t.y * sn);
     zi = fma(t.x, sn, t.y * cs);
 }

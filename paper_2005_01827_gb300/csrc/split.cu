@@ -270,8 +270,10 @@ __device__ __forceinline__ void phasor(unsigned long long ph, const float2 *__re
                                        float &zr, float &zi) {
     const unsigned int hi = (unsigned int)(ph >> 32);
     const float2 t = tab[hi >> 24];
-    const float u = __uint_as_float(0x3f800000u | ((hi << 8) >> 9)) - 1.0f;  // 23 bits in [0,1)
-    const float r = u * 0.024543692606170259f;                              // 2 pi / 256
+    // x in [1, 2) carries the next 23 bits; fmaf(x, step, -step) = (x - 1) step rounded
+    // once, as (x - 1) is exact
+    const float x = __uint_as_float(0x3f800000u | ((hi << 8) >> 9));
+    const float r = fmaf(x, 0.024543692606170259f, -0.024543692606170259f);  // 2 pi / 256
     const float r2 = r * r;
     const float sn = r * fmaf(r2, -0.16666666666666666f, 1.0f);
     const float cs = fmaf(r2, fmaf(r2, 0.041666666666666664f, -0.5f), 1.0f);
