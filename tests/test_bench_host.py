@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py that decides whether a measurement stands: the clock and
+throttle-reason summary taken from nvidia-smi samples during the timed region, and the
+whole-job throughput arithmetic.  No GPU and no nvidia-smi needed."""
+import threading
+
+import bench
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.proc = _FakeProc()
+    s.thread = threading.Thread(target=lambda: None)
+    s.thread.start()
+    s.lines = list(lines)
+    return s
+
+
+def test_clock_summary_median_and_reasons():
+    lines = [
+        "2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1310.4, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "[N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    out = _sampler(lines).stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_flags_thermal_and_hw_slowdown():
+    lines = ["1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active"] * 4
+    out = _sampler(lines).stop()
+    assert out["sm_mhz"] == 1500.0
+    assert out["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_nvidia_smi():
+    s = bench.ClockSampler(0)
+    out = s.stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_job_value_is_whole_job_over_slowest_rank():
+    # 4 ranks x 1024 walkers x 10 steps in 2 s (the slowest rank) = 20480 evals/s
+    assert bench.job_value(4, 1024, 10, 2000.0) == 20480.0
+    assert bench.max_over_ranks(1, 3.5) == 3.5
