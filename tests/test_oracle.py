@@ -307,6 +307,104 @@ def test_response_polarisation_symmetry(orc):
     assert np.array_equal(orc.transfer(th4, 2, 2, f, t), T0)
 
 
+def test_delay_phase_is_the_roemer_delay(orc):
+    """The SSB -> constellation-centre phase equals -2 pi f times the arrival delay
+    t_L - t of the wave at the centre.  Two independent sources of that delay: the
+    sampler oracle's frame conversion (its own orbit and sky vectors), and k.p0 from
+    the orbit with the propagation direction k = -(cos b cos l, cos b sin l, sin b)."""
+    rng = np.random.default_rng(11)
+    for _ in range(12):
+        th = W.theta_table2(1).copy()
+        th[7] = rng.uniform(0.0, 2 * math.pi)
+        th[8] = math.asin(rng.uniform(-1.0, 1.0))
+        th[9] = rng.uniform(0.0, math.pi)
+        t = rng.uniform(0.0, 3.15576e7)
+        f = 10 ** rng.uniform(-5.0, -1.0)
+        tL = orc.ssb_to_lisa(t, th[7], th[8], th[9])[0]
+        ph = orc.delay_phase(th, f, t)
+        assert abs(ph - (-2 * math.pi * f * (tL - t))) <= 1e-9 * abs(2 * math.pi * f * R_S)
+        p0, _ = orc.orbit(t)
+        k = -np.array([math.cos(th[8]) * math.cos(th[7]), math.cos(th[8]) * math.sin(th[7]),
+                       math.sin(th[8])])
+        assert abs(ph + 2 * math.pi * f * (k @ p0)) <= 1e-12 * abs(2 * math.pi * f * R_S)
+    # at 0.1 Hz a source in the ecliptic plane along the Earth-Sun line has |phase| ~ 2 pi f AU
+    th = W.theta_table2(1).copy()
+    th[7], th[8] = 0.0, 0.0
+    assert abs(abs(orc.delay_phase(th, 0.1, 0.0)) - 2 * math.pi * 0.1 * R_S) < 1e-9 * R_S
+
+
+def _link_by_quadrature(P, k, f, xs, xr, t_r):
+    """Fractional frequency shift of the link s -> r for light received at xr at t_r
+    from a plane wave h_ij(t, x) = P_ij exp(2 pi i f (t - k.x)), positions frozen:
+    y = -1/2 n.(integral of dh/dt along the light path).n, by 64-point Gauss-Legendre
+    (no closed form of the path integral is used)."""
+    Lsr = np.linalg.norm(xr - xs)
+    n = (xr - xs) / Lsr
+    z, wq = np.polynomial.legendre.leggauss(64)
+    tau = t_r - 0.5 * Lsr * (1.0 - z)            # emission t_r - L .. reception t_r
+    x = xs[None, :] + np.outer(tau - (t_r - Lsr), n)
+    dh = 2j * math.pi * f * (n @ P @ n) * np.exp(2j * math.pi * f * (tau - x @ k))
+    return -0.5 * 0.5 * Lsr * np.sum(wq * dh)
+
+
+def _tdi_time_domain(P, k, f, pos, t):
+    """First-generation X, Y, Z at time t from explicitly delayed links: the round
+    trip a -> b -> a received at a at t is y_{b->a}(t) + y_{a->b}(t - L), and
+    X = [0->2->0](t) - [0->1->0](t) - [0->2->0](t - 2L) + [0->1->0](t - 2L), Y and Z
+    by cyclic permutation of the spacecraft.  Times are taken relative to t (the wave's
+    phase origin there), which keeps the large phase 2 pi f t out of the rounding."""
+    L = np.linalg.norm(pos[1] - pos[0])
+
+    def rt(a, b, tt):
+        return (_link_by_quadrature(P, k, f, pos[b], pos[a], tt) +
+                _link_by_quadrature(P, k, f, pos[a], pos[b], tt - L))
+
+    def mich(a, b, c):
+        return rt(a, c, t) - rt(a, b, t) - rt(a, c, t - 2 * L) + rt(a, b, t - 2 * L)
+
+    return mich(0, 1, 2), mich(1, 2, 0), mich(2, 0, 1)
+
+
+@pytest.mark.parametrize("fL", [0.05, 0.3, 0.83, 1.7])
+def test_response_matches_time_domain_tdi_at_finite_fL(orc, fL):
+    """Eqs. (7)-(10) at finite f L against a time-domain computation for a frozen
+    constellation: a monochromatic plane wave with the mode's polarisation factors,
+    each link integrated along the light path, X, Y, Z formed with explicit L delays,
+    then A, E, T.  With the spacecraft offsets q relative to the centre this is the
+    transfer; with the absolute positions p0 + q it is the transfer times
+    exp(i delay phase).  This fixes the sinc argument, the sign of the link exponent,
+    the delay operators and the sign of the delay phase at finite f L.  (f L = 1/2,
+    1, 3/2, ... are avoided: there 1 - D^2 = 0 and every first-generation channel
+    vanishes.)"""
+    f = fL / L_S
+    rng = np.random.default_rng(int(fL * 1000))
+    for l, m in ((2, 2), (3, 3), (2, 1)):
+        th = W.theta_table2(1).copy()
+        th[5], th[6] = rng.uniform(0, 2 * math.pi), rng.uniform(0.2, 2.9)
+        th[7], th[8] = rng.uniform(0, 2 * math.pi), math.asin(rng.uniform(-1, 1))
+        th[9] = rng.uniform(0, math.pi)
+        t = rng.uniform(0.0, 3.15576e7)
+        T = orc.transfer(th, l, m, np.array([f]), np.array([t]))[:, 0]
+        p0, q = orc.orbit(t)
+        Ep, Ec = _pol_tensors(th[7], th[8], th[9])
+        Yp = _ylm_table(l, m, th[6], th[5])
+        Ym = _ylm_table(l, -m, th[6], th[5])
+        Kp = 0.5 * (Ym + (-1) ** l * np.conj(Yp))
+        Kc = 0.5j * (Ym - (-1) ** l * np.conj(Yp))
+        P = Kp * Ep + Kc * Ec
+        k = -np.array([math.cos(th[8]) * math.cos(th[7]), math.cos(th[8]) * math.sin(th[7]),
+                       math.sin(th[8])])
+        scale = np.abs(T).max()
+        assert scale > 0
+        for pos, rot in ((q, 1.0), (p0[None, :] + q, np.exp(1j * orc.delay_phase(th, f, t)))):
+            X, Y, Z = _tdi_time_domain(P, k, f, pos, 0.0)
+            A = (Z - X) / math.sqrt(2)
+            E = (X - 2 * Y + Z) / math.sqrt(6)
+            Tc = (X + Y + Z) / math.sqrt(3)
+            want = np.array([A, E, Tc])
+            assert np.abs(T * rot - want).max() <= 1e-10 * scale, (l, m, fL)
+
+
 # ----------------------------------------------------------------------------- likelihood
 
 def test_zero_noise_injection_lnL_zero(orc):
