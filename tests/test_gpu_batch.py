@@ -81,9 +81,12 @@ def test_autotune_picks_a_supported_shape_and_keeps_results(pkg, orc):
         like.close()
 
 
-def test_8192_walkers_masses_1e3_to_1e9(pkg, orc):
-    """The 8192-walker workload at full size: graph-captured, autotuned, FP64."""
-    LL = pkg.lisalike
+@pytest.fixture(scope="module")
+def c3_case(orc):
+    """The 8192-walker workload's data and walkers, and the oracle on 128+ of them
+    (the 8 lightest and 8 heaviest, bands at the grid edges, random picks)."""
+    from fullsize import sample_walkers
+
     g = W.GRID_C2
     S = orc.psd_aet(g.freqs())
     inj = W.theta_table2(1)
@@ -91,17 +94,35 @@ def test_8192_walkers_masses_1e3_to_1e9(pkg, orc):
     d = d + orc.noise(S, g.df, W.white_noise(g.n_bins, 2))
     th = W.draw_walkers_c3(8192, 3)
     th[:, 4] = [orc.dl_gpc(z) for z in th[:, 4]]
-    like = pkg.LisaLike(modes=W.MODES6, n_knots=1024, max_batch=8192)
+    idx, n_edge = sample_walkers(orc, th, W.T0_YEAR, W.MODES6, g, seed=1)
+    ref, rdh, rhh, dd = orc.loglike(th[idx], W.T0_YEAR, W.MODES6, 1024, g.f0, g.df, d, S)
+    return g, S, d, th, idx, n_edge, ref, rhh, dd
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_8192_walkers_masses_1e3_to_1e9(pkg, c3_case, split):
+    """The 8192-walker workload at full size: graph-captured, autotuned, FP64 and split
+    precision, against the oracle on the sampled walkers."""
+    LL = pkg.lisalike
+    g, S, d, th, idx, n_edge, ref, rhh, dd = c3_case
+    assert idx.size >= 128
+    prec = pkg.LISA_PREC_SPLIT if split else pkg.LISA_PREC_FP64
+    like = pkg.LisaLike(modes=W.MODES6, n_knots=1024, max_batch=8192, precision=prec)
     like.set_data(g.f0, g.df, g.n_bins, d, S)
     LL.lisa_like_autotune(like.h, th[:256], 256)
     LL.lisa_like_set_graphs(like.h, True)
     lnL, dh, hh = like.loglike(th)
+    again, _, _ = like.loglike(th)          # replay of the captured graph
     like.close()
-    assert np.all(np.isfinite(lnL))
+    assert np.all(np.isfinite(lnL)) and np.array_equal(again, lnL)
     m = th[:, 0]
-    idx = np.unique(np.concatenate([np.argsort(m)[:3], np.argsort(m)[-3:], [0, 4096, 8191]]))
-    ref, rdh, rhh, dd = orc.loglike(th[idx], W.T0_YEAR, W.MODES6, 1024, g.f0, g.df, d, S)
     scale = np.maximum(np.maximum(rhh, dd), 1.0)
     err = np.abs(lnL[idx] - ref) / scale
-    print("8192-walker sampled max |d lnL| / SNR^2 = %.3e (masses %s)" % (err.max(), m[idx]))
+    sig = rhh > 1e-6
+    rel_hh = np.abs(hh[idx] - rhh)[sig] / rhh[sig]
+    print("8192-walker %s, %d walkers (%d at grid edges, masses %.3g..%.3g): max |d lnL| / "
+          "SNR^2 = %.3e, max |d lnL| = %.3e, max rel d<h|h> = %.3e"
+          % ("split" if split else "fp64", idx.size, n_edge, m[idx].min(), m[idx].max(),
+             err.max(), np.abs(lnL[idx] - ref).max(), rel_hh.max()))
     assert np.all(err <= 1e-6)
+    assert np.all(rel_hh <= 1e-6)

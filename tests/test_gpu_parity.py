@@ -250,6 +250,44 @@ def test_bounded_wait_reports_timeout_and_handle_recovers(pkg, orc):
     like.close()
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_device_wait_gives_up_and_handle_recovers(pkg, orc, split):
+    """The dense kernels' bounded wait on the staging barrier: with the test switch the
+    barrier is armed but no copy is issued, so every wait gives up after 64 polls with
+    nothing in flight.  The host call returns LISA_ERR_TIMEOUT, the device call leaves
+    NaN outputs, and the next normal call on the same handle (also under graph replay)
+    is correct again."""
+    import torch
+
+    from paper_2005_01827_gb300 import lisalike as LL
+
+    g, th, S, d = c1_setup(orc)
+    prec = pkg.LISA_PREC_SPLIT if split else pkg.LISA_PREC_FP64
+    like = pkg.LisaLike(modes=[(2, 2)], n_knots=256, t0=W.T0_C1, max_batch=4, precision=prec)
+    like.set_data(g.f0, g.df, g.n_bins, d, S)
+    P = np.stack([th, th * np.array([1.0005] + [1.0] * 10)])
+    ref, _, _ = like.loglike(P)
+    for graphs in (False, True):
+        LL.lisa_like_set_graphs(like.h, graphs)
+        LL.lisa_like_test_device_wait(like.h, 64)
+        with pytest.raises(LL.LisaError) as e:
+            like.loglike(P)
+        assert e.value.status == LL.LISA_ERR_TIMEOUT
+        dp = torch.tensor(P, dtype=torch.float64, device="cuda")
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        st = torch.cuda.Stream()
+        LL.lisa_like_loglike_device(like.h, dp, 2, out, None, None, st.cuda_stream)
+        st.synchronize()
+        assert np.all(np.isnan(out.cpu().numpy()))
+        LL.lisa_like_test_device_wait(like.h, 0)
+        again, _, _ = like.loglike(P)
+        assert np.array_equal(again, ref)
+    with pytest.raises(LL.LisaError) as e:
+        LL.lisa_like_test_device_wait(like.h, -1)
+    assert e.value.status == LL.LISA_ERR_ARG
+    like.close()
+
+
 def test_device_api_matches_host_api_and_is_deterministic(pkg, orc):
     import torch
 
@@ -284,21 +322,35 @@ def c2_data(orc):
 
 
 def test_c2_full_size_sampled_walkers(pkg, orc, c2_data):
-    """1024 walkers, 6 modes, K = 1024, 3.16e6 bins (the benchmark launch); the oracle
-    recomputes a sample of walkers one by one."""
+    """1024 walkers, 6 modes, K = 1024, 3.16e6 bins (the benchmark launch) in FP64 and in
+    split precision; the oracle recomputes 128+ walkers one by one (the lightest, the
+    heaviest, bands at the grid edges, random picks)."""
+    from fullsize import sample_walkers
+
     g, S, d, inj = c2_data
     th = walkers(orc, 1024, 1)
     th[0] = inj
-    like = pkg.LisaLike(modes=W.MODES6, n_knots=1024, max_batch=1024)
-    like.set_data(g.f0, g.df, g.n_bins, d, S)
-    lnL, dh, hh = like.loglike(th)
-    assert np.all(np.isfinite(lnL))
-    idx = np.array([0, 1, 2, 100, 511, 777, 1000, 1023])
+    idx, n_edge = sample_walkers(orc, th, W.T0_YEAR, W.MODES6, g)
+    idx = np.union1d(idx, [0])
+    assert idx.size >= 128
     ref, rdh, rhh, dd = orc.loglike(th[idx], W.T0_YEAR, W.MODES6, 1024, g.f0, g.df, d, S)
     scale = np.maximum(dd, rhh)
-    err = np.abs(lnL[idx] - ref) / scale
-    print("C2 sampled max |d lnL| / SNR^2 = %.3e" % err.max())
-    assert np.all(err <= 1e-6)
-    snr_inj = math.sqrt(hh[0])
-    assert 200 < snr_inj < 2000
-    like.close()
+    for prec in (pkg.LISA_PREC_FP64, pkg.LISA_PREC_SPLIT):
+        like = pkg.LisaLike(modes=W.MODES6, n_knots=1024, max_batch=1024, precision=prec)
+        like.set_data(g.f0, g.df, g.n_bins, d, S)
+        pkg.lisalike.lisa_like_autotune(like.h, th[:256], 256)
+        lnL, dh, hh = like.loglike(th)
+        like.close()
+        assert np.all(np.isfinite(lnL))
+        err = np.abs(lnL[idx] - ref) / scale
+        sig = rhh > 1e-6
+        rel_hh = np.abs(hh[idx] - rhh)[sig] / rhh[sig]
+        print("C2 %s, %d walkers (%d at grid edges): max |d lnL| / SNR^2 = %.3e, max |d lnL| "
+              "= %.3e, max rel d<h|h> = %.3e" % ("fp64" if prec == pkg.LISA_PREC_FP64 else "split",
+                                                 idx.size, n_edge, err.max(),
+                                                 np.abs(lnL[idx] - ref).max(), rel_hh.max()))
+        assert np.all(err <= 1e-6)
+        assert rel_hh.max() <= 1e-6
+        if prec == pkg.LISA_PREC_FP64:
+            snr_inj = math.sqrt(hh[0])
+            assert 200 < snr_inj < 2000
