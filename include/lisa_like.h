@@ -163,13 +163,23 @@ lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls);
  * B * (ceil(n_bins / 1024) + 1) <= LISA_NOALLOC_MAX_ITEMS; larger requests return
  * LISA_ERR_ARG, and lisa_like_last_error(NULL) on the same thread says which limit.
  * The first call on a device looks up the scratch address on that device (with it
- * current), so make that first call before any stream capture.  Every call shares the
+ * current), so make that first call before any stream capture.  The address is kept
+ * for the life of the process: resetting a device (cudaDeviceReset) or re-creating its
+ * primary context after the first call is not supported.  Every call shares the
  * one scratch array and leaves its contents behind: calls that overlap on the GPU
  * (different streams or host threads) race and must be serialised by the caller. */
 lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, double f0, double df,
                                       int64_t n_bins, const double *d_bins, double dd,
                                       const double *d_params, int B, double *d_lnL,
                                       double *d_dh, double *d_hh, void *stream);
+
+/* Test of the device-side timeout path (the paper has no counterpart).  With polls > 0
+ * the dense kernels of later calls on this handle arm each data tile's barrier for the
+ * tile's bytes but issue no copy, so every wait on it gives up after `polls` polls with
+ * no copy in flight: the call then returns LISA_ERR_TIMEOUT (loglike) or NaN outputs
+ * (loglike_device), exactly as when a real staging copy never completes.  polls = 0
+ * restores normal operation.  Errors: LISA_ERR_ARG for polls outside [0, 2^20]. */
+lisa_status lisa_like_test_device_wait(lisa_like_t *h, int polls);
 
 /* Capture the whole per-call kernel sequence in a CUDA graph (on = 1) and replay it.
  * The executable is cached for the last (B, parameter and output pointers) and

@@ -43,6 +43,10 @@ struct StageBufs {
     int *counter;          // dense work-queue counter
     int *err;              // set by a device wait that gave up
     double *part;          // [items][G][2] per-item, per-slot partial sums
+    // Test only (0 in normal operation): when > 0 the dense kernels arm each tile's
+    // barrier for the tile's bytes but issue no copy, so every wait on it gives up after
+    // this many polls, with no copy in flight, and takes the error path.
+    unsigned wait_test_polls = 0;
 };
 
 struct DenseTune {

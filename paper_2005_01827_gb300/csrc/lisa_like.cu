@@ -73,6 +73,7 @@ struct lisa_like {
     // tile shapes chosen by lisa_like_autotune, per (n_bins, K, precision)
     std::map<std::tuple<int, int, int>, DenseTune> tuned;
     bool profiling = false;
+    unsigned wait_test_polls = 0;      // lisa_like_test_device_wait
     lisa::RbState *rb = nullptr;       // relative binning (lisa_like_set_fiducial)
     std::vector<cudaEvent_t> prof_ev;  // kProfEvents events per profiled call
     int prof_calls = 0;
@@ -180,6 +181,7 @@ StageBufs bufs_of(const lisa_like_t *h, const double *params) {
     b.counter = h->counter;
     b.err = h->err_flag;
     b.part = h->part;
+    b.wait_test_polls = h->wait_test_polls;
     return b;
 }
 
@@ -781,6 +783,14 @@ lisa_status lisa_like_read_profile(lisa_like_t *h, double *ms, int *n_calls) {
             ms[i] += t;
         }
     h->prof_calls = 0;
+    return LISA_OK;
+}
+
+lisa_status lisa_like_test_device_wait(lisa_like_t *h, int polls) {
+    if (!h) return LISA_ERR_ARG;
+    if (polls < 0 || polls > (1 << 20)) return fail(h, LISA_ERR_ARG, "polls must be in [0, 2^20]");
+    h->wait_test_polls = (unsigned)polls;
+    drop_graph(h);  // a captured graph holds the previous setting
     return LISA_OK;
 }
 

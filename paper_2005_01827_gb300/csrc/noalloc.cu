@@ -25,7 +25,12 @@ using namespace lisa;
 namespace {
 
 constexpr size_t kScratchBytes = LISA_NOALLOC_SCRATCH_BYTES;
-constexpr int kTile = 1024;  // 128 threads x 8 bins, the dense kernel's tile
+// The dense kernel's fixed shape here: 128 threads x 8 bins per tile, one walker per
+// group.  The item bound and the partial-sum buffer below are derived from it.
+constexpr int kThreads = 128, kPerThread = 8, kGroup = 1;
+constexpr int kTile = kThreads * kPerThread;
+static_assert(kTile == 1024, "the limit LISA_NOALLOC_MAX_ITEMS is stated for 1024-bin tiles");
+static_assert(kGroup == 1, "the item bound counts one (item, walker) slot per walker and tile");
 
 // The scratch of every no-alloc call on this device.  It is part of the library's
 // device image, so every GPU that loads the library holds it until the process exits.
@@ -181,7 +186,7 @@ extern "C" lisa_status lisa_like_loglike_noalloc(const lisa_like_config *cfg, do
         d.ml[i] = i < L ? cfg->modes[i][0] : 0;
         d.mm[i] = i < L ? cfg->modes[i][1] : 0;
     }
-    const DenseTune tune = {128, 8, nsm * 2, 1};
+    const DenseTune tune = {kThreads, kPerThread, nsm * 2, kGroup};
     cudaStream_t s = (cudaStream_t)stream;
     // Every buffer is written before it is read within the call; the work counter and the
     // error flag, the only values that must start at zero, are cleared by the planning

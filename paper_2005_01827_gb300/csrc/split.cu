@@ -381,9 +381,12 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
         // by plain loads, so nothing past the end of the data is read
         const int full = (Jend - J0) & ~3, tail = Jend - J0 - full;
         if (tid == 0 && full > 0) {
+            const uint32_t bytes = (uint32_t)(full * kBinFloats * sizeof(float));
             fence_proxy_async();
-            tma_load_1d(sbin, bins + (size_t)J0 * kBinFloats,
-                        (uint32_t)(full * kBinFloats * sizeof(float)), bar);
+            if (b.wait_test_polls == 0)
+                tma_load_1d(sbin, bins + (size_t)J0 * kBinFloats, bytes, bar);
+            else
+                mbar_expect_tx(bar, bytes);  // test of the give-up path: no copy is issued
         }
         if (tid < tail * kBinFloats)
             sbin[full * kBinFloats + tid] = bins[((size_t)J0 + full) * kBinFloats + tid];
@@ -416,7 +419,8 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
         __syncthreads();
         if (full > 0) {
             // every thread waits; the block leaves together if the copy never completed
-            if (!__syncthreads_and(mbar_wait_bounded(bar, parity, b.err))) return;
+            const uint32_t polls = b.wait_test_polls ? b.wait_test_polls : kWaitPolls;
+            if (!__syncthreads_and(mbar_wait_bounded(bar, parity, b.err, polls))) return;
             parity ^= 1u;
         }
 

@@ -23,6 +23,13 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// arm the barrier for `bytes` of transaction without issuing a copy
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // arm the barrier for `bytes` of transaction and issue one bulk copy global -> shared.
 // dst and src must be 16-byte aligned and bytes a multiple of 16.
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
@@ -50,9 +57,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // wait for the barrier phase with `parity`; false (and the error flag set) if it does not
-// complete within kWaitPolls polls
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err) {
-    for (uint32_t i = 0; i < kWaitPolls; i++)
+// complete within `polls` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  uint32_t polls = kWaitPolls) {
+    for (uint32_t i = 0; i < polls; i++)
         if (mbar_try_wait(bar, parity)) return true;
     atomicExch(err, 1);
     return false;

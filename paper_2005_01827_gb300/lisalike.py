@@ -29,7 +29,7 @@ SYMBOLS = (
     "lisa_like_stage_knots", "lisa_like_stage_coeffs", "lisa_dl_from_z", "lisa_psd_aet",
     "lisa_like_last_launches", "lisa_like_destroy", "lisa_like_last_error",
     "lisa_like_set_profiling", "lisa_like_read_profile", "lisa_like_loglike_noalloc",
-    "lisa_like_set_graphs", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
+    "lisa_like_set_graphs", "lisa_like_test_device_wait", "lisa_like_set_tune", "lisa_like_get_tune", "lisa_like_autotune",
     "lisa_like_mode_inner", "lisa_like_mode_cross", "lisa_like_set_fiducial", "lisa_like_rb_edges",
     "lisa_like_loglike_rb", "lisa_like_loglike_rb_device",
     # include/lisa_sampler.h
@@ -154,6 +154,8 @@ def load(path: str = LIB_PATH):
     ip = C.POINTER(C.c_int)
     L.lisa_like_set_graphs.argtypes = [vp, i]
     L.lisa_like_set_graphs.restype = i
+    L.lisa_like_test_device_wait.argtypes = [vp, i]
+    L.lisa_like_test_device_wait.restype = i
     L.lisa_like_set_tune.argtypes = [vp, i, i]
     L.lisa_like_set_tune.restype = i
     L.lisa_like_get_tune.argtypes = [vp, ip]
@@ -246,6 +248,17 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _require_device_f64(t, n, name):
+    """A tensor handed to an entry point that takes raw device addresses must be a
+    contiguous float64 CUDA tensor of at least n elements (None passes)."""
+    if t is None or not hasattr(t, "data_ptr"):
+        return
+    if str(t.dtype) != "torch.float64" or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {n}")
+
+
 def _check(st, h=None):
     if st != LISA_OK:
         raise LisaError(st, lisa_like_last_error(h))
@@ -329,7 +342,13 @@ def lisa_like_read_profile(h):
 
 def lisa_like_loglike_noalloc(cfg, f0, df, n_bins, d_bins, dd, d_params, B, d_lnL, d_dh=None,
                               d_hh=None, stream=None):
-    """Allocation-free batched ln L on caller-owned device buffers (see the header)."""
+    """Allocation-free batched ln L on caller-owned device buffers (see the header).
+
+    Tensor arguments must be contiguous float64 CUDA tensors at least as large as the
+    call reads or writes: the C entry point only sees their addresses."""
+    for t, need, name in ((d_bins, 9 * int(n_bins), "d_bins"), (d_params, 11 * int(B), "d_params"),
+                          (d_lnL, int(B), "d_lnL"), (d_dh, int(B), "d_dh"), (d_hh, int(B), "d_hh")):
+        _require_device_f64(t, need, name)
     s = None if stream is None else C.c_void_p(int(stream))
     _check(load().lisa_like_loglike_noalloc(C.byref(cfg), f0, df, n_bins, _ptr(d_bins), dd,
                                             _ptr(d_params), B, _ptr(d_lnL), _ptr(d_dh),
@@ -338,6 +357,12 @@ def lisa_like_loglike_noalloc(cfg, f0, df, n_bins, d_bins, dd, d_params, B, d_ln
 
 def lisa_like_set_graphs(h, on: bool):
     _check(load().lisa_like_set_graphs(h, int(bool(on))), h)
+
+
+def lisa_like_test_device_wait(h, polls: int):
+    """Test of the device-side timeout path: later calls arm the staging barrier without
+    a copy and give up after `polls` polls (0 = normal operation)."""
+    _check(load().lisa_like_test_device_wait(h, int(polls)), h)
 
 
 def lisa_like_set_tune(h, per_thread: int, group: int):
