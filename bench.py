@@ -39,14 +39,20 @@ WORKLOAD = ("1024 walkers, 6 modes (2,2),(3,3),(4,4),(2,1),(3,2),(4,3), K=1024 k
 WORKLOAD_C3 = ("8192 walkers with M_T log-uniform in [1e3, 1e9] Msun, 6 modes, K=1024 knots, "
                "1-yr grid (3155445 bins), A/E/T, FP64, CUDA-graph replay, autotuned tiles, "
                "Binary-1 injection + seeded noise")
-# algorithmic work (see the design notes): per (walker, mode, active bin) 8 cubic Horner
-# evaluations (48), the segment offset (1), the t_coal ramp (2), e^{i phi} (18: a table
-# entry rotated by sine and cosine polynomials of the remaining angle, r = (x - 1) step as
-# one FMA, sine to r^5, cosine to r^4 with a fitted r^4 coefficient), A e^{i phi} (2),
-# three complex transfer products accumulated into the mode sum (24) = 95 flops; per
-# (walker, bin) f_j (2) and the three-channel integrand (27) = 29 flops.
-FLOP_MODE_BIN = 48 + 1 + 2 + 18 + 2 + 24
-FLOP_BIN = 29
+# Algorithmic work per unit, the count the roofline's `achieved` uses: per (walker, mode,
+# active bin) Horner for the 8 series (24 FMA = 48 flops), A e^{i phi} (2), three complex
+# products T A e^{i phi} (12 as FMA + mul) and 6 adds into the channel sums, about 75
+# flops, plus one sincos counted apart (not as flops); per (walker, bin) the three-channel
+# integrand Re(d h*) w and |h|^2 w with its partial-sum add, about 25 flops.
+FLOP_MODE_BIN = 75
+FLOP_BIN = 25
+# The implementation's own count of what the kernels execute, reported beside it: the
+# phase series' Horner is replaced by the exact recurrence, and per (walker, mode, bin) it
+# adds the segment offset (1), the t_coal ramp (2) and the table-plus-polynomial phasor
+# (18) and spends 24 on the complex products = 95 flops; per (walker, bin) f_j (2) and
+# the integrand (27) = 29 flops.
+IMPL_FLOP_MODE_BIN = 48 + 1 + 2 + 18 + 2 + 24
+IMPL_FLOP_BIN = 29
 # data bytes streamed per bin by a walker tile (w and w*d for A, E, T, FP64) and the
 # spline coefficients per segment (8 series x 4 doubles)
 BYTES_BIN = 72
@@ -312,15 +318,25 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
+    impl = impl_count(mode_bins, bins, dense_ms, peak)
     tpw = TRAFFIC_SPLIT_PER_WALKER_BIN.get(tuple(shape[:2]))
+    traffic = tpw * bins if tpw else None
     probe = lisalike.probe_pipes(torch.cuda.current_device())
     return {"value": job_value(world, B, args.steps, ms), "unit": "evals/s",
             "ms_per_step": ms / args.steps, "dtype": "f32+f64", "graphs": graphs,
             "tile": {"bins_per_thread": shape[0], "group": shape[1], "blocks": shape[2]},
             "roofline": {"bound": "alu", "kernel": "dense_split_kernel", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": tpw * bins if tpw else None,
+                         "frac_survey_count": achieved / peak, "implementation_count": impl,
+                         "sincos_per_s": mode_bins / (dense_ms * 1e-3),
+                         "traffic": traffic,
                          "traffic_unit": "bytes per launch",
+                         "hbm_gbs": traffic / (dense_ms * 1e-3) / 1e9 if traffic else None,
+                         "algorithmic_bytes": algo_bytes(bins, shape[1], B, coef_bytes=192, bin_bytes=36),
+                         "traffic_over_algorithmic":
+                             traffic / algo_bytes(bins, shape[1], B, coef_bytes=192, bin_bytes=36)
+                             if traffic else None,
+                         "units_per_launch": {"walker_mode_bins": mode_bins, "walker_bins": bins},
                          "fractions": {
                              "binding": "fp32 (issue)", "fp32": achieved / peak,
                              "fp64": None, "mufu": None,
@@ -791,6 +807,20 @@ def run_rb(args, world, rank, local):
     return 0
 
 
+def algo_bytes(walker_bins, group, B, L=6, K=1024, coef_bytes=256, bin_bytes=None):
+    """Algorithmic HBM bytes of one dense launch: the data row of each bin streamed once
+    per walker group, and every (walker, mode) spline segment's record once."""
+    return (bin_bytes or BYTES_BIN) * walker_bins / group + coef_bytes * B * L * (K - 1)
+
+
+def impl_count(mode_bins, bins, dense_ms, peak):
+    """The dense kernel's rate by the implementation's own flop count (labelled figure
+    beside the algorithmic one)."""
+    a = (IMPL_FLOP_MODE_BIN * mode_bins + IMPL_FLOP_BIN * bins) / (dense_ms * 1e-3) / 1e12
+    return {"flop_per_walker_mode_bin": IMPL_FLOP_MODE_BIN, "flop_per_walker_bin": IMPL_FLOP_BIN,
+            "achieved": a, "frac": a / peak}
+
+
 def profile_once(lisalike, like, step):
     """Per-stage CUDA-event times of one call (profiling off afterwards)."""
     lisalike.lisa_like_set_profiling(like.h, True)
@@ -929,18 +959,24 @@ def main():
     flops = FLOP_MODE_BIN * mode_bins + FLOP_BIN * bins
     achieved = flops / (dense_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
+    impl = impl_count(mode_bins, bins, dense_ms, peak)
     tpw = TRAFFIC_F64_PER_WALKER_BIN.get(tuple(shape[:2]))
     traffic = tpw * bins if tpw else None
     probe = lisalike.probe_pipes(local)      # measured pipe rates of this device
     roofline = {"bound": "alu", "kernel": "dense_f64_kernel", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "unit": "TFLOP/s", "frac": achieved / peak, "frac_survey_count": achieved / peak,
+                "implementation_count": impl, "sincos_per_s": mode_bins / (dense_ms * 1e-3),
+                "traffic": traffic,
                 "traffic_unit": "bytes per launch",
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "units_per_launch": {"walker_mode_bins": mode_bins, "walker_bins": bins},
                 "stage_ms_per_call": {k: v / max(ncalls, 1) for k, v in
                                       zip(("knots", "splines", "segprep", "plan", "dense",
                                            "finish"), stage_ms)},
-                "hbm_gbs": BYTES_BIN * bins / (dense_ms * 1e-3) / 1e9,
+                "hbm_gbs": traffic / (dense_ms * 1e-3) / 1e9 if traffic else None,
+                "algorithmic_bytes": algo_bytes(bins, shape[1], B),
+                "traffic_over_algorithmic": traffic / algo_bytes(bins, shape[1], B)
+                if traffic else None,
                 "hbm_peak_gbs": peaks().get("hbm_gbs"),
                 "measured_pipes": {"fp64_tflops": 2 * probe["fp64_fma_per_s"] / 1e12,
                                    "fp32_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
