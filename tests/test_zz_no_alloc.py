@@ -94,16 +94,24 @@ def test_noalloc_matches_handle_entry_point_full_grid(env, orc):
 
 
 def test_noalloc_rejects_requests_beyond_its_limits(env):
+    """Each rejected request is sized so that, were the limit check ever loosened, the
+    call would still stay inside its buffers (a failure, not an out-of-bounds access)."""
     torch, LL = env
     cfg = LL.lisa_like_default_config()          # six modes, K = 1024
-    g = W.GRID_C2
-    bins = torch.zeros((16, 9), dtype=torch.float64, device="cuda")
+    g = W.Grid(1e-4, 1e-6, 64)
+    bins = torch.zeros((g.n_bins, 9), dtype=torch.float64, device="cuda")
     P = torch.zeros((2, 11), dtype=torch.float64, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     with pytest.raises(LL.LisaError) as e:      # 2 x 6 x 1024 > 8192
         LL.lisa_like_loglike_noalloc(cfg, g.f0, g.df, g.n_bins, bins, 0.0, P, 2, out)
     assert e.value.status == LL.LISA_ERR_ARG and "8192" in str(e.value)
-    cfg.n_modes, cfg.n_knots = 1, 64
-    with pytest.raises(LL.LisaError) as e:      # 6 x (3082 + 1) items > 16384
-        LL.lisa_like_loglike_noalloc(cfg, g.f0, g.df, g.n_bins, bins, 0.0, P, 6, out)
+    cfg.n_modes, cfg.n_knots = 1, 4
+    B, n_bins = 2048, 8192                       # 2048 x 4 knots = 8192 (allowed)
+    bins = torch.zeros((n_bins, 9), dtype=torch.float64, device="cuda")
+    P = torch.zeros((B, 11), dtype=torch.float64, device="cuda")
+    out = torch.zeros(B, dtype=torch.float64, device="cuda")
+    with pytest.raises(LL.LisaError) as e:      # 2048 x (9 + 1) items > 16384
+        LL.lisa_like_loglike_noalloc(cfg, 1e-4, 1e-6, n_bins, bins, 0.0, P, B, out)
     assert e.value.status == LL.LISA_ERR_ARG and "16384" in str(e.value)
+    with pytest.raises(ValueError):             # a short output buffer never reaches C
+        LL.lisa_like_loglike_noalloc(cfg, 1e-4, 1e-6, 64, bins, 0.0, P, B, out[:8])
