@@ -33,7 +33,8 @@ struct StageBufs {
     int *kb;               // [B][L][K]: first dense bin with f_j >= f_k
     double *vals;          // [B][L][8][K]
     double *mscratch;      // [B][L][11][K]: spline second derivatives of the 8 series, then
-                           // the shared factorisation (1/h, 1/pivot, normalised super-diagonal)
+                           // the shared factorisation: 1/h (row 8) and the normalised
+                           // super-diagonal (row 10); row 9 is spare
     double *coef;          // [B][L][K-1][8][4]
     int *wrange;           // [B][2] union of the walker's active mode ranges
     int *order;            // [B] walkers sorted by band (groups are runs of G entries)
@@ -49,6 +50,23 @@ struct StageBufs {
     unsigned wait_test_polls = 0;
 };
 
+// Split precision keeps the phase series in FP64 (row 1 of vals and of the second
+// derivatives in mscratch, as in FP64) and the seven other series in FP32 inside the same
+// per-(walker, mode) storage: series q' = 0 (A 2^64) and 1..6 (Re, Im of T^A, T^E, T^T)
+// as FP32 rows of K values from double row 2 of vals (knot values) and of mscratch
+// (second derivatives), and FP32 copies of 1/h, h, 1/pivot and the normalised
+// super-diagonal as four FP32 rows from double row 6 of mscratch.
+constexpr int kSplitSeries32 = 7;
+__host__ __device__ inline float *split_vals32(double *vals, size_t wm, int K) {
+    return reinterpret_cast<float *>(vals + (wm * 8 + 2) * (size_t)K);
+}
+__host__ __device__ inline float *split_m32(double *mscratch, size_t wm, int K) {
+    return reinterpret_cast<float *>(mscratch + (wm * kScratchRows + 2) * (size_t)K);
+}
+__host__ __device__ inline float *split_fac32(double *mscratch, size_t wm, int K) {
+    return reinterpret_cast<float *>(mscratch + (wm * kScratchRows + 6) * (size_t)K);
+}
+
 struct DenseTune {
     int threads;     // threads per block
     int per_thread;  // consecutive bins per thread
@@ -63,13 +81,17 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 // the band kernel alone (walker constants, peak, bands; no knots)
 cudaError_t launch_band(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s);
+// split precision: FP64 phase, FP32 amplitude and transfer (layout above)
+cudaError_t launch_knots_split(const StageDims &d, const StageBufs &b, cudaStream_t s);
+cudaError_t launch_spline_split(const StageDims &d, const StageBufs &b, cudaStream_t s);
 cudaError_t launch_plan(const StageDims &d, const StageBufs &b, int tile_bins, int group,
                         cudaStream_t s);
 // Fixed-point phase record of one spline segment (kPhaseWords words): the full phase
 // phi - 2 pi f t_coal and its first three forward differences over one bin at the
 // segment's first bin, as fractions of a turn scaled by 2^64 (words 0..3), and the next
 // 64 fractional bits of the three differences (words 4..6), which keep anchors deep
-// inside long segments exact to the FP64 value of the differences; word 7 is padding.
+// inside long segments exact to the FP64 value of the differences; the low 32 bits of
+// word 7 hold the first bin of the next segment (0x7fffffff for the last one).
 constexpr int kPhaseWords = 8;
 
 // FP64 path: the phase records of all segments ([B][L][K-1][kPhaseWords]).

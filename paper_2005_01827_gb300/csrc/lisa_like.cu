@@ -323,9 +323,9 @@ lisa_status enqueue(lisa_like_t *h, const double *dparams, int B, double *lnL, d
     const int tile = h->tune.threads * h->tune.per_thread;
     const bool split = h->precision == LISA_PREC_SPLIT;
     LCK(mark(0), "cudaEventRecord");
-    LCK(launch_knots(d, b, s), "knot kernel launch");
+    LCK(split ? launch_knots_split(d, b, s) : launch_knots(d, b, s), "knot kernel launch");
     LCK(mark(1), "cudaEventRecord");
-    LCK(launch_spline(d, b, s), "spline kernel launch");
+    LCK(split ? launch_spline_split(d, b, s) : launch_spline(d, b, s), "spline kernel launch");
     LCK(mark(2), "cudaEventRecord");
     if (split)
         LCK(launch_segprep(d, b, h->segs, s), "segment kernel launch");

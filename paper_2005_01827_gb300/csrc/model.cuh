@@ -439,4 +439,12 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
     out[2] = cscale(cadd(cadd(X, Y), Z), r3);
 }
 
+// ---------------------------------------------------------------- split precision
+// The split-precision knot stage evaluates everything in FP64 like the FP64 path and
+// stores the amplitude (times 2^64, far from the FP32 underflow) and the transfer as FP32;
+// only the phase series stays FP64.  (Evaluating A and T in FP32 at the knots was tried:
+// errors at a knot are common to the whole segment, so they average far less than the
+// per-bin FP32 errors of the dense stage, and |d lnL| at SNR 1000 grew about tenfold.)
+constexpr double kAmpScale64 = 18446744073709551616.0;  // 2^64
+
 }  // namespace lisa

@@ -21,11 +21,13 @@
 namespace lisa {
 
 namespace {
+// Cody-Waite three-part split of 2 pi for the exact reduction of a knot phase to a
+// fraction of a turn: a head with few significant bits (so k x head is exact for the
+// multiples k that occur), then the FP64 middle and tail of the remainder.
 constexpr double kTwoPiHi = 6.2831854820251465;        // FP32-exact leading part of 2 pi
 constexpr double kTwoPiMid = -1.748455600074497e-07;   // 2 pi - hi
 constexpr double kTwoPiLo = -1.0687562935444062e-23;   // 2 pi - hi - mid
 constexpr double kInvTwoPi = 0.15915494309189535;
-constexpr double kAmpScale = 18446744073709551616.0;    // 2^64: keeps A in FP32 range
 }  // namespace
 
 // fraction of a turn of x radians as a 128-bit two's-complement fixed-point number:
@@ -77,7 +79,10 @@ cudaError_t launch_prep_split(const double *bins, int N, float *out, cudaStream_
 // ------------------------------------------------------------------------ segments
 // One thread per (walker, mode, segment): FP32 cubics of A 2^64 and the six transfer
 // components in t = (j - kb_s) / W_s over the segment's W_s bins, and the fixed-point
-// forward differences of the full phase at its first bin.
+// forward differences of the full phase at its first bin.  With kFull (split precision)
+// the amplitude and transfer cubics come from their FP32 knot values and second
+// derivatives, the phase from its FP64 spline coefficients; without it (the FP64 path)
+// only the phase record is made.
 template <bool kFull>
 __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, SegRec *segs,
                                                       unsigned long long *phases) {
@@ -103,6 +108,29 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
         int slot = 0;
         for (int q = 0; q < kNSeries; q++) {
             if (!kFull && q != 1) continue;
+            if (q != 1) {
+                // FP32 cubic of series q in t from its knot values and second derivatives:
+                // the spline's x-polynomial on [f_s, f_s+1) re-expanded at x = a and scaled
+                // to t (x = a + t W df)
+                const int q32 = (q == 0) ? 0 : q - 1;
+                const float *yv = split_vals32(b.vals, wm, K) + (size_t)q32 * K;
+                const float *Mv = split_m32(b.mscratch, wm, K) + (size_t)q32 * K;
+                const float *f32 = split_fac32(b.mscratch, wm, K);
+                const float ihs = f32[s], hs = f32[K + s];
+                const float ys = yv[s], ys1 = yv[s + 1], ms = Mv[s], ms1 = Mv[s + 1];
+                const float e1 = (ys1 - ys) * ihs - hs * fmaf(2.0f, ms, ms1) * (1.0f / 6.0f);
+                const float e2 = 0.5f * ms;
+                const float e3 = (ms1 - ms) * ihs * (1.0f / 6.0f);
+                const float af = (float)a, wf = (float)wd;
+                const int base = slot == 0 ? 0 : 4 + 8 * ((slot - 1) >> 1) + ((slot - 1) & 1);
+                const int step = slot == 0 ? 1 : 2;
+                r.c[base] = fmaf(af, fmaf(af, fmaf(af, e3, e2), e1), ys);
+                r.c[base + step] = fmaf(af, fmaf(3.0f * af, e3, 2.0f * e2), e1) * wf;
+                r.c[base + 2 * step] = fmaf(3.0f * af, e3, e2) * wf * wf;
+                r.c[base + 3 * step] = e3 * wf * wf * wf;
+                slot++;
+                continue;
+            }
             const double c0 = cf[4 * q], c1 = cf[4 * q + 1], c2 = cf[4 * q + 2], c3 = cf[4 * q + 3];
             const double y = fma(a, fma(a, fma(a, c3, c2), c1), c0);
             const double y1 = fma(a, fma(3.0 * a, c3, 2.0 * c2), c1);
@@ -118,18 +146,8 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
                 turns_fixed(p1 + p2 + p3, r.ph[1], r.ph[4]);
                 turns_fixed(2.0 * p2 + 6.0 * p3, r.ph[2], r.ph[5]);
                 turns_fixed(6.0 * p3, r.ph[3], r.ph[6]);
-                r.ph[7] = 0;
-                continue;
+                r.ph[7] = (unsigned int)((s < K - 2) ? kb[s + 1] : 0x7fffffff);
             }
-            // A at c[0..3]; Re and Im of each channel's transfer interleaved after it
-            const double sc = (q == 0) ? kAmpScale : 1.0;
-            const int base = slot == 0 ? 0 : 4 + 8 * ((slot - 1) >> 1) + ((slot - 1) & 1);
-            const int step = slot == 0 ? 1 : 2;
-            r.c[base] = (float)(sc * y);
-            r.c[base + step] = (float)(sc * y1 * wd);
-            r.c[base + 2 * step] = (float)(sc * y2 * wd * wd);
-            r.c[base + 3 * step] = (float)(sc * c3 * wd * wd * wd);
-            slot++;
         }
         if (kFull) {
             r.kb0 = kb0;
@@ -215,28 +233,35 @@ struct PhaseState {
     unsigned long long ph, d1, d2, d3;
 };
 
-// forward differences of the segment's phase moved from its first bin to bin n
-// (Newton's forward-difference formula, exact in modular integer arithmetic; for n >= 0
-// the low words add the carries of the 128-bit products)
+// floor(c L / 2^64) from the top 32 bits of L: low by less than c / 2^32 + 2 (c < 2^63)
+__device__ __forceinline__ unsigned long long mulhi_top32(unsigned long long c,
+                                                          unsigned long long L) {
+    const unsigned int lh = (unsigned int)(L >> 32);
+    return (c >> 32) * lh + (((unsigned long long)(unsigned int)c * lh) >> 32);
+}
+
+// forward differences of the segment's phase moved from its first bin to bin n >= 0
+// (Newton's forward-difference formula in modular integer arithmetic).  The carries of
+// the low words into the phase and the first difference are taken from their top 32
+// bits and the ones multiplied by n are dropped: the anchor is low by at most a few n
+// units of 2^-64 turn, below 2^-38 turn along any chunk for n < 2^21.
 __device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, int n) {
     const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(rp->ph);
     const ulonglong2 a = __ldg(w), b = __ldg(w + 1);
-    const long long nn = n;
-    const unsigned long long c1 = (unsigned long long)nn;
-    // n(n-1) >= 0 and even; n(n-1)(n-2)/2 is a multiple of 3, so multiplying by the
-    // inverse of 3 modulo 2^64 divides it exactly
-    const unsigned long long c2 = (unsigned long long)(nn * (nn - 1)) >> 1;
-    const unsigned long long c3 = (c2 * (unsigned long long)(nn - 2)) * 0xAAAAAAAAAAAAAAABull;
+    const unsigned int un = (unsigned int)n;
+    // n(n-1)/2 and n(n-1)(n-2)/6 (the product of three consecutive integers divided by 2
+    // is a multiple of 3: multiplying by the inverse of 3 modulo 2^64 divides it exactly)
+    const unsigned long long c2 = ((unsigned long long)un * (un - 1u)) >> 1;
+    const unsigned long long c3 = (c2 * (unsigned long long)(un - 2u)) * 0xAAAAAAAAAAAAAAABull;
     PhaseState p;
-    p.ph = a.x + c1 * a.y + c2 * b.x + c3 * b.y;
-    p.d1 = a.y + c1 * b.x + c2 * b.y;
-    p.d2 = b.x + c1 * b.y;
+    p.ph = a.x + a.y * un + c2 * b.x + c3 * b.y;
+    p.d1 = a.y + b.x * un + c2 * b.y;
+    p.d2 = b.x + b.y * un;
     p.d3 = b.y;
-    if (n > 0) {
+    if (n >= 2) {
         const ulonglong2 c = __ldg(w + 2), e = __ldg(w + 3);
-        p.ph += __umul64hi(c1, c.x) + __umul64hi(c2, c.y) + __umul64hi(c3, e.x);
-        p.d1 += __umul64hi(c1, c.y) + __umul64hi(c2, e.x);
-        p.d2 += __umul64hi(c1, e.x);
+        p.ph += mulhi_top32(c2, c.y) + mulhi_top32(c3, e.x);
+        p.d1 += mulhi_top32(c2, e.x);
     }
     return p;
 }
@@ -447,9 +472,18 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 const size_t wm = (size_t)w * d.L + mi;
                 const int *kb = b.kb + wm * K;
                 const SegRec *sg = segs + wm * (K - 1);
-                int s = seg_guess(kb, K, ja, fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
+                int s = (int)(__log2f(__fdividef(fmaf((float)ja, dff, f0f), s_flo[k][mi])) *
+                              s_scl[k][mi]);
+                s = min(max(s, 0), K - 2);
                 SegCoef r = seg_coef(sg + s);
-                int knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
+                int knext = (int)__ldg(&sg[s].ph[7]);
+                // the record of the guessed segment is loaded with the bounds that check it,
+                // so a right guess (the usual case) costs no dependent load
+                if ((s > 0 && r.kb0 > ja) || knext <= ja) {  // the guess missed: search
+                    s = seg_guess(kb, K, ja, fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
+                    r = seg_coef(sg + s);
+                    knext = (int)__ldg(&sg[s].ph[7]);
+                }
                 PhaseState p = phase_at(sg + s, ja - r.kb0);
                 const float ta = (float)(ja - r.kb0) * r.invw;
                 float2 tt = make_float2(ta, ta);  // (t, t): the packed Horner operand
@@ -475,7 +509,7 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                     if (j >= knext) {  // the chunk crosses into the next segment
                         s++;
                         r = seg_coef(sg + s);
-                        knext = (s < K - 2) ? __ldg(kb + s + 1) : 0x7fffffff;
+                        knext = (int)__ldg(&sg[s].ph[7]);
                         p = phase_at(sg + s, j - r.kb0);
                         const float tj = (float)(j - r.kb0) * r.invw;
                         tt = make_float2(tj, tj);

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(128) band_kernel(StageDims d, StageBufs b) {
 // ---------------------------------------------------------------------------- knots
 // One block per (walker, mode): thread 0 rebuilds the walker constants (the stored peak
 // spares the bisection) and the source frame; all threads then fill the K log-spaced
-// knots (Sec. II.A: ~2^10 points) with A, phase + delay, and T.
+// knots (Sec. II.A: ~2^10 points) with A, phase + delay, and T.  kSplit: the same FP64
+// values, A (times 2^64) and T stored as FP32 (the split-precision layout).
+template <bool kSplit>
 __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
     const int wm = blockIdx.x;
     const int w = wm / d.L, mi = wm % d.L;
@@ -111,6 +113,20 @@ __global__ void __launch_bounds__(128) knot_kernel(StageDims d, StageBufs b) {
         while (j > 0 && bin_freq(d.f0, d.df, j - 1) >= f) j--;
         while (j < d.N && bin_freq(d.f0, d.df, j) < f) j++;
         kbm[k] = j;
+        if (kSplit) {
+            double amp, ph, t, dly;
+            mode_all(src, md, f, amp, ph, t);
+            cplx T[3];
+            tdi_transfer(frame, kp, kc, f, t, T, &dly);
+            vm[1 * K + k] = ph + dly;
+            float *v32 = split_vals32(b.vals, wm, K);
+            v32[k] = (float)(amp * kAmpScale64);
+            for (int c = 0; c < 3; c++) {
+                v32[(1 + 2 * c) * K + k] = (float)T[c].re;
+                v32[(2 + 2 * c) * K + k] = (float)T[c].im;
+            }
+            continue;
+        }
         double amp, ph, t;
         mode_all(src, md, f, amp, ph, t);
         cplx T[3];
@@ -136,7 +152,15 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
     band_kernel<<<(d.B * d.L + 127) / 128, 128, 0, s>>>(d, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    knot_kernel<<<d.B * d.L, 128, 0, s>>>(d, b);
+    knot_kernel<false><<<d.B * d.L, 128, 0, s>>>(d, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knots_split(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    band_kernel<<<(d.B * d.L + 127) / 128, 128, 0, s>>>(d, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    knot_kernel<true><<<d.B * d.L, 128, 0, s>>>(d, b);
     return cudaGetLastError();
 }
 
@@ -146,46 +170,139 @@ cudaError_t launch_knots(const StageDims &d, const StageBufs &b, cudaStream_t s)
 // 8 series of one (walker, mode) share the matrix.  A block owns 32 systems and every
 // lane one system, so the serial recurrences keep all 32 lanes busy (GB300's FP64 pipe
 // spends a full warp's time on every FP64 instruction whatever the active mask): warp 0
-// factorises the 32 matrices, warp q sweeps series q of the 32 systems; a second,
+// factorises the 32 matrices, warp q sweeps series q of the 32 systems.
+//
+// The recurrences run over chunks of kCh knots staged in shared memory: the whole block
+// loads a chunk of every input row of its 32 systems with coalesced accesses (threads
+// walk consecutive knots of one row), transposed so that lane s reads system s; warp 0
+// factorises the chunk, the eight warps sweep it, and the block writes the chunk's
+// outputs back the same coalesced way.  (Walking each system's rows directly from
+// global memory made every warp access touch 32 rows, and the solve waited on memory.)
+// The arithmetic and its order are those of the plain recurrences.  A second,
 // grid-stride kernel emits the per-segment coefficients.  The factorisation lives in
 // global scratch rows next to the second derivatives.
 constexpr int kSplineSystems = 32;
+constexpr int kCh = 16;                     // knots per staged chunk
+constexpr int kPad = kSplineSystems + 1;    // row pitch of a transposed tile
+constexpr int kTile = kCh * kPad;           // elements of one [kCh][kPad] tile
 
-// The three serial recurrences (factorisation, forward and backward sweeps) load their
-// inputs in chunks of kChunk knots ahead of the dependent arithmetic, so that the loads of
-// a chunk are in flight together instead of one per step; the arithmetic is unchanged.
-constexpr int kChunk = 8;
+// Shared memory of the solve: x, the 8 FP64 series values (outputs written in place)
+// and the factorisation chunk (1/h, h, 1/pivot, normalised super-diagonal) in FP64; in
+// split precision also 7 FP32 series tiles and the FP32 copies of the factorisation.
+template <bool kSplit>
+constexpr size_t spline_smem() {
+    return sizeof(double) * kTile * (1 + kNSeries + 4) +
+           (kSplit ? sizeof(float) * kTile * (kSplitSeries32 + 4) : 0);
+}
 
+// Coalesced transposed copies between kCh consecutive entries [i0, i0 + kCh) of one row
+// per system and a [kCh][kPad] tile (entry k of system s at tile[k * kPad + s]); rows of
+// systems outside the call or inactive are skipped, and so are indices >= iend.
+template <typename T>
+__device__ __forceinline__ void tile_load(T *tile, const T *base, size_t pitch, int i0, int iend,
+                                          const int *act) {
+    for (int e = threadIdx.x; e < kSplineSystems * kCh; e += blockDim.x) {
+        const int s = e / kCh, k = e % kCh, i = i0 + k;
+        if (act[s] && i < iend) tile[k * kPad + s] = base[s * pitch + i];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store(const T *tile, T *base, size_t pitch, int i0, int iend,
+                                           const int *act) {
+    for (int e = threadIdx.x; e < kSplineSystems * kCh; e += blockDim.x) {
+        const int s = e / kCh, k = e % kCh, i = i0 + k;
+        if (act[s] && i < iend) base[s * pitch + i] = tile[k * kPad + s];
+    }
+}
+
+// kSplit: warp 0 also writes FP32 copies of the factorisation; series 1 (the phase) is
+// swept in FP64, the other seven in FP32 (the split-precision layout).  FP32 sweeps: the
+// second differences lose bits in FP32, but the interpolant depends on M only through
+// terms of order h^2 M, far below the values.
+template <bool kSplit>
 __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
+    extern __shared__ __align__(16) unsigned char spl_sm[];
     const int K = d.K, n = K;
+    const size_t KK = (size_t)K;
     const int nsys = d.B * d.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wm = blockIdx.x * kSplineSystems + lane;
-    const bool mine = wm < nsys && b.band[(size_t)wm * 3];
-    const double *__restrict__ x = b.fk + (size_t)wm * K;
-    double *Mv = b.mscratch + (size_t)wm * kScratchRows * K;
-    double *__restrict__ ih = Mv + (size_t)kNSeries * K;  // 1 / h
-    double *__restrict__ dinv = ih + K;                   // 1 / pivot
-    double *__restrict__ cpr = dinv + K;                  // normalised super-diagonal
-    if (warp == 0 && mine) {
-        double hprev = x[1] - x[0], hcur;
-        const double ih0 = 1.0 / hprev;
-        ih[0] = ih0;
-        double cprev = 0.0;
-        double ihprev = ih0;  // 1 / h_{i-1}
-        double xi = x[1];
-        for (int i0 = 1; i0 <= n - 2; i0 += kChunk) {
-            double xn[kChunk];
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) xn[k] = (i0 + k <= n - 2) ? x[i0 + k + 1] : 0.0;
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) {
-                const int i = i0 + k;
-                if (i > n - 2) break;
-                hcur = xn[k] - xi;
-                xi = xn[k];
+    const size_t wm0 = (size_t)blockIdx.x * kSplineSystems;
+    const size_t wm = wm0 + lane;
+    __shared__ int act[kSplineSystems];
+    if (threadIdx.x < kSplineSystems) {
+        const size_t w2 = wm0 + threadIdx.x;
+        act[threadIdx.x] = (w2 < (size_t)nsys && b.band[w2 * 3]) ? 1 : 0;
+    }
+    double *xs = reinterpret_cast<double *>(spl_sm);         // x[i + 1]
+    double *ys = xs + kTile;                                  // [8] y[i + 1], then M[i]
+    double *fs = ys + kNSeries * kTile;                       // [4] 1/h, h, 1/pivot, cpr
+    float *ys32 = reinterpret_cast<float *>(fs + 4 * kTile);  // split: [7]
+    float *fs32 = ys32 + kSplitSeries32 * kTile;              // split: [4]
+    __syncthreads();
+    const bool mine = act[lane] != 0;
+    const int q = warp;  // series swept by this warp
+    const bool f32s = kSplit && q != 1;
+    const int q32 = (q == 0) ? 0 : q - 1;
+    // row bases of the block's first system and the pitches between systems
+    const double *xg = b.fk + wm0 * KK;
+    const double *yg = b.vals + wm0 * kNSeries * KK;
+    double *Mg = b.mscratch + wm0 * kScratchRows * KK;
+    const size_t pY = kNSeries * KK, pM = kScratchRows * KK;
+    const float *y32g = kSplit ? split_vals32(b.vals, wm0, K) : nullptr;
+    float *M32g = kSplit ? split_m32(b.mscratch, wm0, K) : nullptr;
+    float *F32g = kSplit ? split_fac32(b.mscratch, wm0, K) : nullptr;
+    const size_t pY32 = 2 * pY, pM32 = 2 * pM;  // the same pitches in floats
+
+    // per-lane set-up from the lane's own rows
+    double hprev = 0.0, ihp = 0.0, cprev = 0.0, xi = 0.0;           // factorisation
+    double prev = 0.0, dprev = 0.0, ylast = 0.0, hlast = 0.0, ihl = 0.0;
+    float prevf = 0.0f, dprevf = 0.0f, ylastf = 0.0f, hlastf = 0.0f, ihlf = 0.0f;
+    if (mine) {
+        const double *x = b.fk + wm * KK;
+        const double h0 = x[1] - x[0];
+        const double ih0 = 1.0 / h0;
+        if (warp == 0) {
+            hprev = h0;
+            ihp = ih0;
+            xi = x[1];
+            Mg[lane * pM + kNSeries * KK] = ih0;
+            if (kSplit) {
+                F32g[lane * pM32] = (float)ih0;
+                F32g[lane * pM32 + KK] = (float)h0;
+            }
+        }
+        if (f32s) {
+            const float *yq = y32g + lane * pY32 + q32 * KK;
+            dprevf = (yq[1] - yq[0]) * (float)ih0;
+            ylastf = yq[1];
+            hlastf = (float)h0;
+        } else {
+            const double *yq = b.vals + (wm * kNSeries + q) * KK;
+            dprev = (yq[1] - yq[0]) * ih0;
+            ylast = yq[1];
+            hlast = h0;
+        }
+    }
+
+    // factorisation and forward sweeps, chunk by chunk (steps i = 1 .. n - 2)
+    for (int i0 = 1; i0 <= n - 2; i0 += kCh) {
+        const int nk = min(kCh, n - 1 - i0);
+        __syncthreads();
+        tile_load(xs, xg, KK, i0 + 1, n, act);
+        for (int qq = 0; qq < kNSeries; qq++)
+            if (!kSplit || qq == 1) tile_load(ys + qq * kTile, yg + qq * KK, pY, i0 + 1, n, act);
+        if (kSplit)
+            for (int r = 0; r < kSplitSeries32; r++)
+                tile_load(ys32 + r * kTile, y32g + r * KK, pY32, i0 + 1, n, act);
+        __syncthreads();
+        if (warp == 0 && mine) {
+            for (int k = 0; k < nk; k++) {
+                const int i = i0 + k, o = k * kPad + lane;
+                const double xn = xs[o];
+                const double hcur = xn - xi;
+                xi = xn;
                 const double ihc = 1.0 / hcur;
-                ih[i] = ihc;
                 double dia = 2.0 * (hprev + hcur);
                 double sup = hcur;
                 double sb = hprev;
@@ -194,95 +311,161 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
                     sup -= hprev * hprev * ihc;
                 }
                 if (i == n - 2) {
-                    dia += hcur * (hprev + hcur) * ihprev;
-                    sb -= hcur * hcur * ihprev;
+                    dia += hcur * (hprev + hcur) * ihp;
+                    sb -= hcur * hcur * ihp;
                 }
                 const double pv = (i == 1) ? dia : dia - sb * cprev;
                 const double inv = 1.0 / pv;
-                dinv[i] = inv;
                 cprev = sup * inv;
-                cpr[i] = cprev;
                 hprev = hcur;
-                ihprev = ihc;
+                ihp = ihc;
+                fs[o] = ihc;
+                fs[kTile + o] = hcur;
+                fs[2 * kTile + o] = inv;
+                fs[3 * kTile + o] = cprev;
+                if (kSplit) {
+                    fs32[o] = (float)ihc;
+                    fs32[kTile + o] = (float)hcur;
+                    fs32[2 * kTile + o] = (float)inv;
+                    fs32[3 * kTile + o] = (float)cprev;
+                }
             }
         }
-    }
-    __syncthreads();
-    if (mine) {
-        const int q = warp;  // series
-        const double *__restrict__ yq = b.vals + ((size_t)wm * kNSeries + q) * K;
-        double *__restrict__ Mq = Mv + (size_t)q * K;
-        double prev = 0.0;
-        double dprev = (yq[1] - yq[0]) * ih[0];
-        double ylast = yq[1];
-        double xprev = x[0];  // x[i - 1]
-        const double hb_end = x[n - 1] - x[n - 2];
-        const double ih_end = ih[n - 3];
-        for (int i0 = 1; i0 <= n - 2; i0 += kChunk) {
-            double yn[kChunk], ihv[kChunk], dv[kChunk], xv[kChunk];
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) {
-                const int i = i0 + k;
-                const bool in = i <= n - 2;
-                yn[k] = in ? yq[i + 1] : 0.0;
-                ihv[k] = in ? ih[i] : 0.0;
-                dv[k] = in ? dinv[i] : 0.0;
-                xv[k] = in ? x[i] : 0.0;
+        __syncthreads();
+        if (mine && f32s) {
+            float *yt = ys32 + q32 * kTile;
+            for (int k = 0; k < nk; k++) {
+                const int i = i0 + k, o = k * kPad + lane;
+                const float ihv = fs32[o], hv = fs32[kTile + o], dv = fs32[2 * kTile + o];
+                const float yn = yt[o];
+                const float dcur = (yn - ylastf) * ihv;
+                ylastf = yn;
+                const float rhs = 6.0f * (dcur - dprevf);
+                dprevf = dcur;
+                float sb = hlastf;
+                if (i == n - 2) sb -= hv * hv * ihlf;
+                const float rp = (i == 1) ? rhs * dv : (rhs - sb * prevf) * dv;
+                yt[o] = rp;
+                prevf = rp;
+                hlastf = hv;
+                ihlf = ihv;
             }
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) {
-                const int i = i0 + k;
-                if (i > n - 2) break;
-                const double ynext = yn[k];
-                const double dcur = (ynext - ylast) * ihv[k];
-                ylast = ynext;
+        } else if (mine) {
+            double *yt = ys + q * kTile;
+            for (int k = 0; k < nk; k++) {
+                const int i = i0 + k, o = k * kPad + lane;
+                const double ihv = fs[o], hv = fs[kTile + o], dv = fs[2 * kTile + o];
+                const double yn = yt[o];
+                const double dcur = (yn - ylast) * ihv;
+                ylast = yn;
                 const double rhs = 6.0 * (dcur - dprev);
                 dprev = dcur;
-                double sb = xv[k] - xprev;
-                xprev = xv[k];
-                if (i == n - 2) sb -= hb_end * hb_end * ih_end;
-                const double rp = (i == 1) ? rhs * dv[k] : (rhs - sb * prev) * dv[k];
-                Mq[i] = rp;
+                double sb = hlast;
+                if (i == n - 2) sb -= hv * hv * ihl;
+                const double rp = (i == 1) ? rhs * dv : (rhs - sb * prev) * dv;
+                yt[o] = rp;
                 prev = rp;
+                hlast = hv;
+                ihl = ihv;
             }
         }
-        double nxt = Mq[n - 2];
-        for (int i0 = n - 3; i0 >= 1; i0 -= kChunk) {
-            double mv[kChunk], cv[kChunk];
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) {
-                const int i = i0 - k;
-                mv[k] = i >= 1 ? Mq[i] : 0.0;
-                cv[k] = i >= 1 ? cpr[i] : 0.0;
+        __syncthreads();
+        // the chunk's forward values and factorisation rows (tile entry k is step i0 + k)
+        for (int qq = 0; qq < kNSeries; qq++)
+            if (!kSplit || qq == 1) tile_store(ys + qq * kTile, Mg + qq * KK, pM, i0, n - 1, act);
+        tile_store(fs, Mg + kNSeries * KK, pM, i0, n - 1, act);                 // 1/h
+        tile_store(fs + 3 * kTile, Mg + (kNSeries + 2) * KK, pM, i0, n - 1, act);  // cpr
+        if (kSplit) {
+            for (int r = 0; r < kSplitSeries32; r++)
+                tile_store(ys32 + r * kTile, M32g + r * KK, pM32, i0, n - 1, act);
+            tile_store(fs32, F32g, pM32, i0, n - 1, act);                      // 1/h
+            tile_store(fs32 + kTile, F32g + KK, pM32, i0, n - 1, act);         // h
+            tile_store(fs32 + 3 * kTile, F32g + 3 * KK, pM32, i0, n - 1, act); // cpr
+        }
+    }
+
+    // backward sweeps, chunk by chunk from the top (steps i = n - 3 .. 1)
+    __syncthreads();
+    double nxt = 0.0;
+    float nxtf = 0.0f;
+    if (mine) {
+        if (f32s)
+            nxtf = M32g[lane * pM32 + q32 * KK + (n - 2)];
+        else
+            nxt = Mg[lane * pM + q * KK + (n - 2)];
+    }
+    for (int i1 = n - 3; i1 >= 1; i1 -= kCh) {
+        const int lo = max(1, i1 - kCh + 1);  // tile entry k is step lo + k
+        __syncthreads();
+        for (int qq = 0; qq < kNSeries; qq++)
+            if (!kSplit || qq == 1) tile_load(ys + qq * kTile, Mg + qq * KK, pM, lo, i1 + 1, act);
+        tile_load(fs + 3 * kTile, Mg + (kNSeries + 2) * KK, pM, lo, i1 + 1, act);
+        if (kSplit) {
+            for (int r = 0; r < kSplitSeries32; r++)
+                tile_load(ys32 + r * kTile, M32g + r * KK, pM32, lo, i1 + 1, act);
+            tile_load(fs32 + 3 * kTile, F32g + 3 * KK, pM32, lo, i1 + 1, act);
+        }
+        __syncthreads();
+        if (mine && f32s) {
+            float *yt = ys32 + q32 * kTile;
+            for (int i = i1; i >= lo; i--) {
+                const int o = (i - lo) * kPad + lane;
+                nxtf = yt[o] - fs32[3 * kTile + o] * nxtf;
+                yt[o] = nxtf;
             }
-#pragma unroll
-            for (int k = 0; k < kChunk; k++) {
-                const int i = i0 - k;
-                if (i < 1) break;
-                nxt = mv[k] - cv[k] * nxt;
-                Mq[i] = nxt;
+        } else if (mine) {
+            double *yt = ys + q * kTile;
+            for (int i = i1; i >= lo; i--) {
+                const int o = (i - lo) * kPad + lane;
+                nxt = yt[o] - fs[3 * kTile + o] * nxt;
+                yt[o] = nxt;
             }
         }
-        const double h0 = x[1] - x[0], h1 = x[2] - x[1];
-        const double ha = x[n - 2] - x[n - 3], hb = x[n - 1] - x[n - 2];
-        Mq[0] = ((h0 + h1) * Mq[1] - h0 * Mq[2]) * ih[1];
-        Mq[n - 1] = ((ha + hb) * Mq[n - 2] - hb * Mq[n - 3]) * ih[n - 3];
+        __syncthreads();
+        for (int qq = 0; qq < kNSeries; qq++)
+            if (!kSplit || qq == 1) tile_store(ys + qq * kTile, Mg + qq * KK, pM, lo, i1 + 1, act);
+        if (kSplit)
+            for (int r = 0; r < kSplitSeries32; r++)
+                tile_store(ys32 + r * kTile, M32g + r * KK, pM32, lo, i1 + 1, act);
+    }
+    __syncthreads();
+
+    // not-a-knot ends: M_0 and M_{n-1} from their neighbours
+    if (mine) {
+        const double *x = b.fk + wm * KK;
+        if (f32s) {
+            float *Mq = M32g + lane * pM32 + q32 * KK;
+            const float *F = F32g + lane * pM32;  // 1/h, then h
+            const float h0 = F[KK], h1 = F[KK + 1], ha = F[KK + n - 3], hb = F[KK + n - 2];
+            Mq[0] = ((h0 + h1) * Mq[1] - h0 * Mq[2]) * F[1];
+            Mq[n - 1] = ((ha + hb) * Mq[n - 2] - hb * Mq[n - 3]) * F[n - 3];
+        } else {
+            double *Mq = Mg + lane * pM + q * KK;
+            const double *ih = Mg + lane * pM + kNSeries * KK;
+            const double h0 = x[1] - x[0], h1 = x[2] - x[1];
+            const double ha = x[n - 2] - x[n - 3], hb = x[n - 1] - x[n - 2];
+            Mq[0] = ((h0 + h1) * Mq[1] - h0 * Mq[2]) * ih[1];
+            Mq[n - 1] = ((ha + hb) * Mq[n - 2] - hb * Mq[n - 3]) * ih[n - 3];
+        }
     }
 }
 
 // Cubic coefficients of every (system, segment, series) from the second derivatives, as
 // a grid-stride kernel of its own: the blocks of the solve do not divide evenly over the
 // SMs, this FP64 work does.
+// kSplit: only the FP64 phase series (the others stay as FP32 values and second
+// derivatives for the segment records).
+template <bool kSplit>
 __global__ void __launch_bounds__(256) spline_coef_kernel(StageDims d, StageBufs b) {
     const int K = d.K;
-    const long long per_sys = (long long)(K - 1) * kNSeries;
+    const long long per_sys = (long long)(K - 1) * (kSplit ? 1 : kNSeries);
     const long long total = (long long)d.B * d.L * per_sys;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long w2 = t / per_sys;
         const int rem = (int)(t - w2 * per_sys);
         if (!b.band[w2 * 3]) continue;
-        const int sgm = rem / kNSeries, q = rem % kNSeries;
+        const int sgm = kSplit ? rem : rem / kNSeries, q = kSplit ? 1 : rem % kNSeries;
         const double *x2 = b.fk + (size_t)w2 * K;
         const double *M2 = b.mscratch + (size_t)w2 * kScratchRows * K;
         const double *yq = b.vals + ((size_t)w2 * kNSeries + q) * K;
@@ -297,16 +480,29 @@ __global__ void __launch_bounds__(256) spline_coef_kernel(StageDims d, StageBufs
     }
 }
 
-cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+template <bool kSplit>
+cudaError_t launch_spline_t(const StageDims &d, const StageBufs &b, cudaStream_t s) {
     const int nsys = d.B * d.L;
-    spline_kernel<<<(nsys + kSplineSystems - 1) / kSplineSystems, 256, 0, s>>>(d, b);
-    cudaError_t e = cudaGetLastError();
+    const size_t smem = spline_smem<kSplit>();
+    cudaError_t e = cudaFuncSetAttribute(spline_kernel<kSplit>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long total = (long long)nsys * (d.K - 1) * kNSeries;
+    spline_kernel<kSplit><<<(nsys + kSplineSystems - 1) / kSplineSystems, 256, smem, s>>>(d, b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)nsys * (d.K - 1) * (kSplit ? 1 : kNSeries);
     const long long want = (total + 255) / 256, cap = 152LL * 8;  // 8 blocks per SM
     const int blocks = (int)(want < cap ? want : cap);
-    spline_coef_kernel<<<blocks, 256, 0, s>>>(d, b);
+    spline_coef_kernel<kSplit><<<blocks, 256, 0, s>>>(d, b);
     return cudaGetLastError();
+}
+
+cudaError_t launch_spline(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    return launch_spline_t<false>(d, b, s);
+}
+
+cudaError_t launch_spline_split(const StageDims &d, const StageBufs &b, cudaStream_t s) {
+    return launch_spline_t<true>(d, b, s);
 }
 
 // ---------------------------------------------------------------------------- data prep
