@@ -393,6 +393,28 @@ def sampler_cpu_baseline(steps=16):
             "seconds": dt}
 
 
+def _sampler_injection(LL):
+    """Physical parameters of the sampler workload's injection (z mapped to D_L)."""
+    inj = np.array(W.THETA_SAMPLER_Z)
+    inj[4] = LL.lisa_dl_from_z(inj[4])
+    return inj
+
+
+def _sampler_data(LL, like):
+    """Give a handle the sampler workload's data: the injection made by the library plus
+    the seeded noise of Eq. (12) coloured by the stand-in PSD; returns the injection."""
+    g = W.GRID_C2
+    psd = np.empty((3, g.n_bins))
+    LL.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
+    like.set_data(g.f0, g.df, g.n_bins, None, psd)
+    inj = _sampler_injection(LL)
+    h = like.template(inj)
+    z = W.white_noise(g.n_bins, 2)
+    d = h + 0.5 * np.sqrt(psd / g.df) * (z[..., 0] + 1j * z[..., 1])
+    like.set_data(g.f0, g.df, g.n_bins, d, psd)
+    return inj
+
+
 def sampler_setup(args, rank, local):
     """Likelihood with the sampler workload's data, starting walkers, tile shapes."""
     import torch
@@ -402,21 +424,12 @@ def sampler_setup(args, rank, local):
     build.build()
     torch.cuda.set_device(local)
     T, Wk = W.SAMPLER_T, W.SAMPLER_W
-    g = W.GRID_C2
     prec = LL.LISA_PREC_SPLIT if args.precision == "split" else LL.LISA_PREC_FP64
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=T * Wk // 2,
                     device=local, precision=prec, stream=stream.cuda_stream)
-    psd = np.empty((3, g.n_bins))
-    LL.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
-    like.set_data(g.f0, g.df, g.n_bins, None, psd)
-    inj = np.array(W.THETA_SAMPLER_Z)
-    inj[4] = LL.lisa_dl_from_z(inj[4])
-    h = like.template(inj)
-    z = W.white_noise(g.n_bins, 2)
-    d = h + 0.5 * np.sqrt(psd / g.df) * (z[..., 0] + 1j * z[..., 1])
-    like.set_data(g.f0, g.df, g.n_bins, d, psd)
+    inj = _sampler_data(LL, like)
     cfg = LL.lisa_sampler_default_config()
     xc = LL.from_physical(inj, True, W.T0_YEAR)
     scale = np.array([1e-3, 1e-3, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2, 1e-3, 1e-3, 1e-2, 1e-4])
@@ -560,51 +573,74 @@ def run_sampler(args, world, rank, local):
 
 FLOW_METRIC = ("MCMC ESS/s of the coldest chain, flow proposal (8 couplings, bf16) vs plain "
                "stretch moves (8 temps x 256 walkers, 6 modes, A/E/T, 1-yr df)")
+FLOW_WORKLOAD = ("; flow: 8 affine couplings (11-128-128-22, bf16 mma.sync, FP32 accumulate), "
+                 "trained every 500 steps on the coldest chain until the end of burn-in, "
+                 "independence MH on the coldest temperature every step")
 
 
-def run_flow(args, world, rank, local):
-    """Config-5 comparison: the same sampler, start and burn-in with and without flow
-    proposals (trained on the coldest chain every 500 steps until the end of burn-in);
-    value = effective samples per second of the coldest chain with the flow."""
+def sky_mode_occupancy(c, xc7):
+    """Fractions of the coldest-chain samples in each of the 8 LISA-frame sky modes (a
+    longitude quarter-turn from the injection's, times the sign of sin beta_L), quarter
+    q = 0..3 first for the injection's hemisphere, then the other one."""
+    quarter = (np.floor(((c[:, 7] - xc7) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4).astype(int)
+    hemi = (c[:, 8] < 0).astype(int)
+    occ = np.bincount(quarter + 4 * hemi, minlength=8) / max(c.shape[0], 1)
+    return occ.tolist()
+
+
+# periods of the angular sampling coordinates (phi_ref, lambda_L, psi_L): their sample
+# means and widths are taken on the circle (unwrapped around the circular mean)
+ANGLE_PERIODS = {5: 2 * np.pi, 7: 2 * np.pi, 9: np.pi}
+
+
+def circular_stats(c):
+    """Per-coordinate mean and standard deviation of samples c [n, 11], the angles
+    unwrapped around their circular mean first."""
+    c = np.array(c, dtype=np.float64, copy=True)
+    for q, P in ANGLE_PERIODS.items():
+        a = 2 * np.pi * c[:, q] / P
+        m = np.arctan2(np.mean(np.sin(a)), np.mean(np.cos(a))) * P / (2 * np.pi)
+        c[:, q] = m + (c[:, q] - m + P / 2) % P - P / 2
+    return c.mean(axis=0), c.std(axis=0)
+
+
+def flow_compare(args, world, rank, local, burn_plain, steps_plain, burn_flow, steps_flow,
+                 flow_precision):
+    """Config-5 comparison on one GPU: the same sampler, seed and start with and without
+    flow proposals (trained on the coldest chain every 500 steps until the end of the
+    flow arm's burn-in).  With flow_precision "fp64" the flow moves of the timed steps are
+    accepted on an FP64 likelihood (exact FP64 ln L of each flow proposal); burn-in flow
+    moves use the sampler's own likelihood.  Returns the two arms' statistics."""
     import torch
 
     LL, like, stream, x0, prec = sampler_setup(args, rank, local)
     T, Wk = W.SAMPLER_T, W.SAMPLER_W
-    xc7 = float(np.median(x0[0, :, 7]))  # reference longitude for the mode quarters
+    xc = LL.from_physical(_sampler_injection(LL), True, W.T0_YEAR)
     like_flow = None
-    if args.flow_precision == "fp64" and prec != LL.LISA_PREC_FP64:
-        # exact FP64 acceptances for the flow moves, the stretch moves in split precision
+    if flow_precision == "fp64" and prec != LL.LISA_PREC_FP64:
         from paper_2005_01827_gb300 import LisaLike
 
         like_flow = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=Wk,
                              device=local, precision=LL.LISA_PREC_FP64, stream=stream.cuda_stream)
-        g = W.GRID_C2
-        psd = np.empty((3, g.n_bins))
-        LL.lisa_psd_aet(g.f0, g.df, g.n_bins, psd)
-        inj = np.array(W.THETA_SAMPLER_Z)
-        inj[4] = LL.lisa_dl_from_z(inj[4])
-        like_flow.set_data(g.f0, g.df, g.n_bins, None, psd)
-        h = like_flow.template(inj)
-        z = W.white_noise(g.n_bins, 2)
-        d = h + 0.5 * np.sqrt(psd / g.df) * (z[..., 0] + 1j * z[..., 1])
-        like_flow.set_data(g.f0, g.df, g.n_bins, d, psd)
+        _sampler_data(LL, like_flow)
     every = args.train_every
-    burn = max(args.warmup, 2 * every)
-    K = args.steps
     out = {}
     clocks = ClockSampler(local)
     clocks.start()
     for use_flow in (False, True):
+        burn = burn_flow if use_flow else burn_plain
+        K = steps_flow if use_flow else steps_plain
         s = LL.LisaSampler(like, seed=11 + rank)
         if use_flow:
             s.enable_flow(train_every=every, train_iters=400, batch=1024, lr=1e-3, seed=3,
                           freeze_after=burn)
-            if like_flow is not None:
-                s.set_flow_likelihood(like_flow)
         s.set_state(x0)
         t0 = time.perf_counter()
         s.run(burn, record=False)
         burn_s = time.perf_counter() - t0
+        if use_flow and like_flow is not None:
+            s.set_flow_likelihood(like_flow)       # exact FP64 flow acceptances from here
+            s.run(1, record=False)                 # capture the step graph with it
         chain = torch.empty((K, Wk, 11), dtype=torch.float64, device="cuda")
         lch = torch.empty((K, Wk), dtype=torch.float64, device="cuda")
         acc0, _ = s.counts()
@@ -620,23 +656,27 @@ def run_flow(args, world, rank, local):
         acc1, _ = s.counts()
         taus, tau = chain_stats(LL, chain, K, Wk, stream)
         c = chain.cpu().numpy().reshape(-1, 11)
-        # the dominant longitude mode (lambda_L within pi/4 of the median of the samples
-        # nearest the most populated quarter-turn)
-        quarter = np.floor(((c[:, 7] - xc7) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4
+        # the dominant sky mode: the most populated longitude quarter-turn
+        quarter = np.floor(((c[:, 7] - xc[7]) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4
         dom = int(np.bincount(quarter.astype(int), minlength=4).argmax())
         main = c[quarter == dom]
-        r = {"ms_per_step": ms / K,
-             "dominant_mode_fraction": float(main.shape[0] / c.shape[0]),
-             "mean_dominant": main.mean(axis=0).tolist(), "std_dominant": main.std(axis=0).tolist(), "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
+        mean, std = circular_stats(c)
+        mean_d, std_d = circular_stats(main)
+        r = {"burn_in_steps": burn, "steps": K, "ms_per_step": ms / K,
+             "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
              "ess": K * Wk / tau, "ess_per_s": world * K * Wk / tau / (ms * 1e-3),
              "stretch_acceptance_cold": float((acc1 - acc0)[0, 0] / max((acc1 - acc0)[0, 1], 1)),
              "burn_in_s": burn_s, "launches_per_step": s.step_launches(),
-             "mean": c.mean(axis=0).tolist(), "std": c.std(axis=0).tolist()}
+             "mean": mean.tolist(), "std": std.tolist(),
+             "sky_mode_occupancy": sky_mode_occupancy(c, xc[7]),
+             "dominant_mode_fraction": float(main.shape[0] / c.shape[0]),
+             "mean_dominant": mean_d.tolist(), "std_dominant": std_d.tolist()}
         if use_flow:
             f1, n_tr, loss = s.flow_stats()
             r["flow_acceptance"] = float((f1 - f0)[0] / max((f1 - f0)[1], 1))
             r["trainings"] = n_tr
             r["last_training_loss"] = loss
+            r["flow_likelihood"] = "fp64" if like_flow is not None else args.precision
         out["flow" if use_flow else "plain"] = r
         xs, _, _, _ = s.state()
         s.close()
@@ -646,36 +686,45 @@ def run_flow(args, world, rank, local):
     if like_flow is not None:
         like_flow.close()
     p, f = out["plain"], out["flow"]
-    sd = np.array(p["std"])
-    sdd = np.array(p["std_dominant"])
-    accuracy = {"max_abs_mean_diff_over_std": float(np.max(np.abs(np.array(f["mean"]) -
-                                                                   np.array(p["mean"])) / sd)),
-                "std_ratio_range": [float(np.min(np.array(f["std"]) / sd)),
-                                    float(np.max(np.array(f["std"]) / sd))],
-                "dominant_mode": {
-                    "max_abs_mean_diff_over_std": float(np.max(np.abs(
-                        np.array(f["mean_dominant"]) - np.array(p["mean_dominant"])) / sdd)),
-                    "std_ratio_range": [float(np.min(np.array(f["std_dominant"]) / sdd)),
-                                        float(np.max(np.array(f["std_dominant"]) / sdd))]}}
+    sd, sdd = np.array(p["std"]), np.array(p["std_dominant"])
+    out["posterior_agreement"] = {
+        "max_abs_mean_diff_over_std": float(np.max(np.abs(np.array(f["mean"]) - np.array(p["mean"])) / sd)),
+        "std_ratio_range": [float(np.min(np.array(f["std"]) / sd)), float(np.max(np.array(f["std"]) / sd))],
+        "dominant_mode": {
+            "max_abs_mean_diff_over_std": float(np.max(np.abs(
+                np.array(f["mean_dominant"]) - np.array(p["mean_dominant"])) / sdd)),
+            "std_ratio_range": [float(np.min(np.array(f["std_dominant"]) / sdd)),
+                                float(np.max(np.array(f["std_dominant"]) / sdd))]},
+        "sky_mode_occupancy_abs_diff_max": float(np.max(np.abs(
+            np.array(f["sky_mode_occupancy"]) - np.array(p["sky_mode_occupancy"]))))}
+    out["flow_over_plain_ess_per_s"] = f["ess_per_s"] / p["ess_per_s"]
+    out["roofline"] = roofline
+    out["clocks"] = clk
+    out["gpu_launches"] = steps_plain * p["launches_per_step"] + steps_flow * f["launches_per_step"]
+    return out
+
+
+def run_flow(args, world, rank, local):
+    """Config-5 comparison as its own bench line: value = effective samples per second of
+    the coldest chain with the flow; both arms take --warmup burn-in and --steps timed
+    steps."""
+    burn = max(args.warmup, 2 * args.train_every)
+    r = flow_compare(args, world, rank, local, burn, args.steps, burn, args.steps,
+                     args.flow_precision)
+    f = r["flow"]
     line = {"metric": FLOW_METRIC, "value": f["ess_per_s"], "unit": "effective samples/s",
-            "n_gpus": world, "steps": K, "warmup": burn, "ms_per_step": f["ms_per_step"],
+            "n_gpus": world, "steps": args.steps, "warmup": burn, "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == LL.LISA_PREC_SPLIT else "f64", "data": "synthetic",
+            "dtype": "f32+f64" if args.precision == "split" else "f64", "data": "synthetic",
             "config": {"start": args.start, "flow_precision": args.flow_precision,
-                       "workload": SAMPLER_WORKLOAD + "; flow: 8 affine couplings "
-                       "(11-128-128-22, bf16 mma.sync, FP32 accumulate), trained every 500 "
-                       "steps on the coldest chain until the end of burn-in, independence MH "
-                       "on the coldest temperature every step",
+                       "workload": SAMPLER_WORKLOAD + FLOW_WORKLOAD,
                        "precision": args.precision, "graphs": True,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (data 227 MB, spline coefficients 0.8 GB)"},
-            "flow_over_plain_ess_per_s": f["ess_per_s"] / p["ess_per_s"],
-            "plain": p, "flow": f, "posterior_agreement": accuracy,
-            "roofline": roofline, "gpu_launches": K * (p["launches_per_step"] + f["launches_per_step"]),
-            "clocks": clk,
             "e2e": {"value": f["ess_per_s"], "unit": "effective samples/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                     "note": "device-resident chains; the host reads them once after the run"}}
+    line.update(r)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -866,6 +915,16 @@ def main():
     ap.add_argument("--train-every", type=int, default=500,
                     help="flow workload: steps between flow trainings (500 is the workload; "
                          "smaller only for profiling captures)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the 8192-walker and flow-vs-plain parts")
+    ap.add_argument("--c3-steps", type=int, default=2,
+                    help="timed steps of the 8192-walker part of the default run")
+    ap.add_argument("--flow-burn", type=int, default=2000,
+                    help="burn-in steps of each arm of the flow-vs-plain part")
+    ap.add_argument("--flow-plain-steps", type=int, default=5000,
+                    help="timed steps of the plain arm of the flow-vs-plain part")
+    ap.add_argument("--flow-steps", type=int, default=600,
+                    help="timed steps of the flow arm of the flow-vs-plain part")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -877,13 +936,44 @@ def main():
     if args.workload == "rb":
         return run_rb(args, world, rank, local)
 
+    line = like_line(args, world, rank, local, args.workload == "c3")
+    if world == 1 and args.workload == "c2" and not args.no_extras:
+        # the rest of the metric on the same run: the 8192-walker workload (masses 1e3..1e9,
+        # graph replay, autotuned tiles) in both precisions, and configuration 5's ESS/s
+        # of the flow-proposal sampler against the plain one
+        a3 = argparse.Namespace(**vars(args))
+        a3.steps, a3.warmup = args.c3_steps, 1
+        line["c3"] = like_line(a3, world, rank, local, True)
+        line["flow_vs_plain"] = flow_compare(args, world, rank, local, args.flow_burn,
+                                             args.flow_plain_steps, args.flow_burn,
+                                             args.flow_steps, "fp64")
+        line["flow_vs_plain"]["config"] = {
+            "workload": SAMPLER_WORKLOAD + FLOW_WORKLOAD, "start": "8 sky modes",
+            "likelihood": "split precision for the stretch moves; exact FP64 ln L for the "
+                          "flow moves of the timed steps (burn-in flow moves in split)",
+            "burn_in_steps": args.flow_burn, "plain_timed_steps": args.flow_plain_steps,
+            "flow_timed_steps": args.flow_steps,
+            "reduced": "config 5 as stated; step counts chosen so the default run stays "
+                       "within minutes (the plain arm's chain_over_tau says whether it "
+                       "reaches the 50 tau of Sec. III.C)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def like_line(args, world, rank, local, c3):
+    """The batched ln L workload (1024 walkers, or with c3 the 8192-walker workload under
+    graph replay) timed for args.steps steps after args.warmup: the bench line's dict."""
     import torch
 
     from paper_2005_01827_gb300 import LisaLike, build, lisalike
 
     build.build()
     torch.cuda.set_device(local)
-    c3 = args.workload == "c3"
     B = 8192 if c3 and args.walkers == 1024 else args.walkers
     g = W.GRID_C2
     like = LisaLike(modes=W.MODES6, n_knots=1024, t0=W.T0_YEAR, max_batch=B, device=local)
@@ -1009,13 +1099,8 @@ def main():
                                              mode_bins, bins, graphs=c3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and B == 1024 and not c3:
         line["cpu_baseline"] = cpu_baseline()
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
+    return line
 
-        dist.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":

@@ -57,3 +57,33 @@ def test_job_value_is_whole_job_over_slowest_rank():
     # 4 ranks x 1024 walkers x 10 steps in 2 s (the slowest rank) = 20480 evals/s
     assert bench.job_value(4, 1024, 10, 2000.0) == 20480.0
     assert bench.max_over_ranks(1, 3.5) == 3.5
+
+
+def test_circular_statistics_of_the_sampler_angles():
+    """Widths of phi_ref, lambda_L (period 2 pi) and psi_L (period pi) are taken on the
+    circle: a cloud straddling the wrap has its own small width, not one of order pi."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    c = 0.01 * rng.standard_normal((4000, 11))
+    c[:, 5] = (0.02 * rng.standard_normal(4000)) % (2 * np.pi)
+    c[:, 7] = (6.27 + 0.01 * rng.standard_normal(4000)) % (2 * np.pi)
+    c[:, 9] = (3.13 + 0.02 * rng.standard_normal(4000)) % np.pi
+    m, s = bench.circular_stats(c)
+    assert abs(s[5] - 0.02) < 2e-3 and abs(s[7] - 0.01) < 1e-3 and abs(s[9] - 0.02) < 2e-3
+    assert abs((m[7] - 6.27 + np.pi) % (2 * np.pi) - np.pi) < 1e-3
+    assert abs((m[9] - 3.13 + np.pi / 2) % np.pi - np.pi / 2) < 2e-3
+    assert abs(s[0] - 0.01) < 1e-3           # other coordinates as usual
+
+
+def test_sky_mode_occupancy_bins():
+    import numpy as np
+
+    lam0 = 1.0
+    c = np.zeros((8, 11))
+    for k in range(8):
+        c[k, 7] = (lam0 + (k % 4) * np.pi / 2 + 0.1) % (2 * np.pi)
+        c[k, 8] = 0.3 if k < 4 else -0.3
+    occ = bench.sky_mode_occupancy(c, lam0)
+    assert np.allclose(occ, 1.0 / 8)
+    assert abs(sum(bench.sky_mode_occupancy(c[:3], lam0)) - 1.0) < 1e-12
