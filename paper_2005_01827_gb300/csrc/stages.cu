@@ -207,6 +207,28 @@ __device__ __forceinline__ void tile_load(T *tile, const T *base, size_t pitch, 
     }
 }
 
+// The two tile entries of this thread (blockDim.x = 256 threads, 512 entries), fetched
+// into registers ahead of use and put into the tile later.
+template <typename T>
+__device__ __forceinline__ void tile_fetch(T r[2], const T *base, size_t pitch, int i0, int iend,
+                                           const int *act) {
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const int e = threadIdx.x + j * 256;
+        const int s = e / kCh, k = e % kCh, i = i0 + k;
+        r[j] = (act[s] && i < iend) ? base[s * pitch + i] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_put(T *tile, const T r[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const int e = threadIdx.x + j * 256;
+        tile[(e % kCh) * kPad + e / kCh] = r[j];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void tile_store(const T *tile, T *base, size_t pitch, int i0, int iend,
                                            const int *act) {
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
     const size_t pY32 = 2 * pY, pM32 = 2 * pM;  // the same pitches in floats
 
     // per-lane set-up from the lane's own rows
-    double hprev = 0.0, ihp = 0.0, cprev = 0.0, xi = 0.0;           // factorisation
+    double hprev = 0.0, ihp = 0.0, cprev = 0.0;                     // factorisation
     double prev = 0.0, dprev = 0.0, ylast = 0.0, hlast = 0.0, ihl = 0.0;
     float prevf = 0.0f, dprevf = 0.0f, ylastf = 0.0f, hlastf = 0.0f, ihlf = 0.0f;
     if (mine) {
@@ -265,7 +287,6 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
         if (warp == 0) {
             hprev = h0;
             ihp = ih0;
-            xi = x[1];
             Mg[lane * pM + kNSeries * KK] = ih0;
             if (kSplit) {
                 F32g[lane * pM32] = (float)ih0;
@@ -285,24 +306,56 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
         }
     }
 
-    // factorisation and forward sweeps, chunk by chunk (steps i = 1 .. n - 2)
+    // factorisation and forward sweeps, chunk by chunk (steps i = 1 .. n - 2).  The next
+    // chunk's inputs are fetched into registers while the current chunk is computed;
+    // h_i = x[i+1] - x[i] and 1/h_i of a chunk are formed by all threads at once, so that
+    // the serial factorisation only carries the pivots.
+    __shared__ double xlast[kSplineSystems];  // x[i0] of the current chunk, per system
+    if (warp == 0 && mine) xlast[lane] = b.fk[wm * KK + 1];
+    double rx[2], ry[kNSeries][2];
+    float ry32[kSplitSeries32][2];
+    auto fetch = [&](int i1) {
+        tile_fetch(rx, xg, KK, i1 + 1, n, act);
+#pragma unroll
+        for (int qq = 0; qq < kNSeries; qq++)
+            if (!kSplit || qq == 1) tile_fetch(ry[qq], yg + qq * KK, pY, i1 + 1, n, act);
+        if (kSplit)
+#pragma unroll
+            for (int r = 0; r < kSplitSeries32; r++)
+                tile_fetch(ry32[r], y32g + r * KK, pY32, i1 + 1, n, act);
+    };
+    fetch(1);
     for (int i0 = 1; i0 <= n - 2; i0 += kCh) {
         const int nk = min(kCh, n - 1 - i0);
         __syncthreads();
-        tile_load(xs, xg, KK, i0 + 1, n, act);
+        tile_put(xs, rx);
+#pragma unroll
         for (int qq = 0; qq < kNSeries; qq++)
-            if (!kSplit || qq == 1) tile_load(ys + qq * kTile, yg + qq * KK, pY, i0 + 1, n, act);
+            if (!kSplit || qq == 1) tile_put(ys + qq * kTile, ry[qq]);
         if (kSplit)
-            for (int r = 0; r < kSplitSeries32; r++)
-                tile_load(ys32 + r * kTile, y32g + r * KK, pY32, i0 + 1, n, act);
+#pragma unroll
+            for (int r = 0; r < kSplitSeries32; r++) tile_put(ys32 + r * kTile, ry32[r]);
+        __syncthreads();
+        if (i0 + kCh <= n - 2) fetch(i0 + kCh);
+        for (int e = threadIdx.x; e < kSplineSystems * kCh; e += blockDim.x) {
+            const int s = e / kCh, k = e % kCh;
+            if (!act[s] || k >= nk) continue;
+            const int o = k * kPad + s;
+            const double h = xs[o] - (k == 0 ? xlast[s] : xs[o - kPad]);
+            const double ih = 1.0 / h;
+            fs[o] = ih;
+            fs[kTile + o] = h;
+            if (kSplit) {
+                fs32[o] = (float)ih;
+                fs32[kTile + o] = (float)h;
+            }
+        }
         __syncthreads();
         if (warp == 0 && mine) {
             for (int k = 0; k < nk; k++) {
                 const int i = i0 + k, o = k * kPad + lane;
-                const double xn = xs[o];
-                const double hcur = xn - xi;
-                xi = xn;
-                const double ihc = 1.0 / hcur;
+                const double hcur = fs[kTile + o];
+                const double ihc = fs[o];
                 double dia = 2.0 * (hprev + hcur);
                 double sup = hcur;
                 double sb = hprev;
@@ -319,18 +372,15 @@ __global__ void __launch_bounds__(256) spline_kernel(StageDims d, StageBufs b) {
                 cprev = sup * inv;
                 hprev = hcur;
                 ihp = ihc;
-                fs[o] = ihc;
-                fs[kTile + o] = hcur;
                 fs[2 * kTile + o] = inv;
                 fs[3 * kTile + o] = cprev;
                 if (kSplit) {
-                    fs32[o] = (float)ihc;
-                    fs32[kTile + o] = (float)hcur;
                     fs32[2 * kTile + o] = (float)inv;
                     fs32[3 * kTile + o] = (float)cprev;
                 }
             }
         }
+        if (warp == 1 && act[lane]) xlast[lane] = xs[(nk - 1) * kPad + lane];
         __syncthreads();
         if (mine && f32s) {
             float *yt = ys32 + q32 * kTile;
