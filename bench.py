@@ -578,13 +578,29 @@ FLOW_WORKLOAD = ("; flow: 8 affine couplings (11-128-128-22, bf16 mma.sync, FP32
                  "independence MH on the coldest temperature every step")
 
 
+def sky_mode_index(c, xc7):
+    """Sky mode 0..7 of each sample: quarter-turn of lambda_L from the injection's, plus 4
+    in the hemisphere of negative sin beta_L."""
+    quarter = (np.floor(((c[:, 7] - xc7) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4).astype(int)
+    return quarter + 4 * (c[:, 8] < 0).astype(int)
+
+
+def sky_mode_lnl(c, lnl, xc7):
+    """Largest and median ln L of the samples in each sky mode (None where empty): how
+    much likelihood separates the modes a chain occupies."""
+    m = sky_mode_index(c, xc7)
+    out = []
+    for k in range(8):
+        v = lnl[m == k]
+        out.append([float(v.max()), float(np.median(v))] if v.size else None)
+    return out
+
+
 def sky_mode_occupancy(c, xc7):
     """Fractions of the coldest-chain samples in each of the 8 LISA-frame sky modes (a
     longitude quarter-turn from the injection's, times the sign of sin beta_L), quarter
     q = 0..3 first for the injection's hemisphere, then the other one."""
-    quarter = (np.floor(((c[:, 7] - xc7) % (2 * np.pi)) / (np.pi / 2) + 0.5) % 4).astype(int)
-    hemi = (c[:, 8] < 0).astype(int)
-    occ = np.bincount(quarter + 4 * hemi, minlength=8) / max(c.shape[0], 1)
+    occ = np.bincount(sky_mode_index(c, xc7), minlength=8) / max(c.shape[0], 1)
     return occ.tolist()
 
 
@@ -665,10 +681,13 @@ def flow_compare(args, world, rank, local, burn_plain, steps_plain, burn_flow, s
         r = {"burn_in_steps": burn, "steps": K, "ms_per_step": ms / K,
              "tau_max": tau, "tau": taus, "chain_over_tau": K / tau,
              "ess": K * Wk / tau, "ess_per_s": world * K * Wk / tau / (ms * 1e-3),
+             "tau_note": "a lower bound (ESS an upper bound) while chain_over_tau < 50 "
+                         "(Sec. III.C)",
              "stretch_acceptance_cold": float((acc1 - acc0)[0, 0] / max((acc1 - acc0)[0, 1], 1)),
              "burn_in_s": burn_s, "launches_per_step": s.step_launches(),
              "mean": mean.tolist(), "std": std.tolist(),
              "sky_mode_occupancy": sky_mode_occupancy(c, xc[7]),
+             "sky_mode_lnL_max_median": sky_mode_lnl(c, lch.cpu().numpy().reshape(-1), xc[7]),
              "dominant_mode_fraction": float(main.shape[0] / c.shape[0]),
              "mean_dominant": mean_d.tolist(), "std_dominant": std_d.tolist()}
         if use_flow:

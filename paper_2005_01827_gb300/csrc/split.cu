@@ -379,6 +379,9 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
     __shared__ int s_item, s_walker[G], s_lo[G][kMaxModes], s_hi[G][kMaxModes];
     __shared__ float s_flo[G][kMaxModes], s_scl[G][kMaxModes];
     __shared__ float4 red[G][4];  // per slot, per warp: (ri, ri comp, hh, hh comp)
+    // groups of 8 walkers: every thread's (ri, ri comp, hh, hh comp) per slot, reduced
+    // once per item below instead of by warp shuffles per walker
+    __shared__ float4 part_s[G == 8 ? G * 128 : 1];
     __shared__ int s_skip[G];
     const int tid = threadIdx.x;
     for (int k = tid; k < 256; k += blockDim.x) {
@@ -548,17 +551,45 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 comp = sub2(sub2(t2, sum), y);
                 sum = t2;
             }
-            // FP32 (value, compensation) pairs summed error-free across the warp here and
-            // across the block below; FP64 from the block's partial up
-            float rs = sum.x, hs = sum.y, rl = -comp.x, hl = -comp.y;
-            warp_sum_pair(rs, rl);
-            warp_sum_pair(hs, hl);
-            if ((tid & 31) == 0) red[k][tid >> 5] = make_float4(rs, rl, hs, hl);
+            // FP32 (value, compensation) pairs summed error-free across the block below;
+            // FP64 from the block's partial up
+            if constexpr (G == 8) {
+                part_s[k * 128 + tid] = make_float4(sum.x, -comp.x, sum.y, -comp.y);
+            } else {
+                float rs = sum.x, hs = sum.y, rl = -comp.x, hl = -comp.y;
+                warp_sum_pair(rs, rl);
+                warp_sum_pair(hs, hl);
+                if ((tid & 31) == 0) red[k][tid >> 5] = make_float4(rs, rl, hs, hl);
+            }
         }
-        // one block barrier per item: thread k sums slot k over the warps, error-free
-        // in FP32 (two-sum of the values, compensations added), then once to FP64
+        // one block barrier per item, then error-free FP32 sums (two-sum of the values,
+        // compensations added) of every slot, once to FP64
         __syncthreads();
-        if (tid < G && s_walker[tid] >= 0) {
+        if constexpr (G == 8) {
+            // 16 sums (slot k, quantity q) of the 128 thread pairs, 8 threads each: 16
+            // pairs per thread, then the 8 threads' pairs by shuffles
+            const int grp = tid >> 3, j = tid & 7, k = grp >> 1, q = grp & 1;
+            float ps = 0.0f, pe = 0.0f;
+            if (s_walker[k] >= 0 && !s_skip[k]) {
+                for (int i = 0; i < 16; i++) {
+                    const float4 v = part_s[k * 128 + i * 8 + j];
+                    float t, r;
+                    two_sum(ps, q ? v.z : v.x, t, r);
+                    ps = t;
+                    pe += r + (q ? v.w : v.y);
+                }
+            }
+            for (int o = 4; o > 0; o >>= 1) {
+                const float s2 = __shfl_down_sync(0xffffffffu, ps, o, 8);
+                const float e2 = __shfl_down_sync(0xffffffffu, pe, o, 8);
+                float t, r;
+                two_sum(ps, s2, t, r);
+                ps = t;
+                pe = pe + e2 + r;
+            }
+            if (j == 0 && s_walker[k] >= 0)
+                b.part[2 * ((size_t)item * G + k) + q] = (double)ps + (double)pe;
+        } else if (tid < G && s_walker[tid] >= 0) {
             const size_t slot = (size_t)item * G + tid;
             double a = 0.0, c = 0.0;
             if (!s_skip[tid]) {

@@ -87,3 +87,14 @@ def test_sky_mode_occupancy_bins():
     occ = bench.sky_mode_occupancy(c, lam0)
     assert np.allclose(occ, 1.0 / 8)
     assert abs(sum(bench.sky_mode_occupancy(c[:3], lam0)) - 1.0) < 1e-12
+
+
+def test_sky_mode_lnl_per_mode():
+    import numpy as np
+
+    c = np.zeros((4, 11))
+    c[:, 7] = [1.0, 1.0, 1.0 + np.pi, 1.0]
+    c[:, 8] = [0.2, 0.2, 0.2, -0.2]
+    out = bench.sky_mode_lnl(c, np.array([-3.0, -1.0, -50.0, -7.0]), 1.0)
+    assert out[0] == [-1.0, -2.0] and out[2] == [-50.0, -50.0] and out[4] == [-7.0, -7.0]
+    assert out[1] is None and out[3] is None
