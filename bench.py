@@ -656,7 +656,10 @@ def flow_compare(args, world, rank, local, burn_plain, steps_plain, burn_flow, s
         burn_s = time.perf_counter() - t0
         if use_flow and like_flow is not None:
             s.set_flow_likelihood(like_flow)       # exact FP64 flow acceptances from here
+            if args.flow_screen > 0:
+                s.set_flow_screen(args.flow_screen)
             s.run(1, record=False)                 # capture the step graph with it
+            sent0 = s.flow_screen_count() if args.flow_screen > 0 else 0
         chain = torch.empty((K, Wk, 11), dtype=torch.float64, device="cuda")
         lch = torch.empty((K, Wk), dtype=torch.float64, device="cuda")
         acc0, _ = s.counts()
@@ -696,6 +699,9 @@ def flow_compare(args, world, rank, local, burn_plain, steps_plain, burn_flow, s
             r["trainings"] = n_tr
             r["last_training_loss"] = loss
             r["flow_likelihood"] = "fp64" if like_flow is not None else args.precision
+            if like_flow is not None and args.flow_screen > 0:
+                r["flow_screen_margin"] = args.flow_screen
+                r["fp64_evaluated_fraction"] = (s.flow_screen_count() - sent0) / float(K * Wk)
         out["flow" if use_flow else "plain"] = r
         xs, _, _, _ = s.state()
         s.close()
@@ -938,11 +944,14 @@ def main():
                     help="default workload: skip the 8192-walker and flow-vs-plain parts")
     ap.add_argument("--c3-steps", type=int, default=2,
                     help="timed steps of the 8192-walker part of the default run")
+    ap.add_argument("--flow-screen", type=float, default=0.05,
+                    help="margin in ln L of the split-precision screen of the FP64 flow "
+                         "moves (0: every flow proposal evaluated in FP64)")
     ap.add_argument("--flow-burn", type=int, default=2000,
                     help="burn-in steps of each arm of the flow-vs-plain part")
-    ap.add_argument("--flow-plain-steps", type=int, default=5000,
+    ap.add_argument("--flow-plain-steps", type=int, default=2500,
                     help="timed steps of the plain arm of the flow-vs-plain part")
-    ap.add_argument("--flow-steps", type=int, default=600,
+    ap.add_argument("--flow-steps", type=int, default=2500,
                     help="timed steps of the flow arm of the flow-vs-plain part")
     args = ap.parse_args()
     world, rank, local = dist_init()
@@ -969,12 +978,17 @@ def main():
         line["flow_vs_plain"]["config"] = {
             "workload": SAMPLER_WORKLOAD + FLOW_WORKLOAD, "start": "8 sky modes",
             "likelihood": "split precision for the stretch moves; exact FP64 ln L for the "
-                          "flow moves of the timed steps (burn-in flow moves in split)",
+                          "flow moves of the timed steps (burn-in flow moves in split); "
+                          "timed flow moves screened by the split ln L with margin %g "
+                          "(the chain of unscreened FP64 flow moves, FP64 work only for "
+                          "the proposals not rejected by the screen)" % args.flow_screen,
             "burn_in_steps": args.flow_burn, "plain_timed_steps": args.flow_plain_steps,
             "flow_timed_steps": args.flow_steps,
             "reduced": "config 5 as stated; step counts chosen so the default run stays "
-                       "within minutes (the plain arm's chain_over_tau says whether it "
-                       "reaches the 50 tau of Sec. III.C)"}
+                       "within minutes; both arms take the same number of timed steps, "
+                       "since tau estimates of chains shorter than 50 tau grow with the "
+                       "chain length (chain_over_tau says how far each arm is from the "
+                       "50 tau of Sec. III.C)"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -155,6 +155,22 @@ lisa_flow_t *lisa_sampler_get_flow(lisa_sampler_t *s);
  * sampler's own.  Requires lisa_sampler_enable_flow. */
 lisa_status lisa_sampler_set_flow_likelihood(lisa_sampler_t *s, lisa_like_t *like2);
 
+/* Screen the flow moves (margin > 0, in ln L units; 0 turns the screen off).  Every flow
+ * proposal is first evaluated by the sampler's own likelihood; a proposal whose
+ * Metropolis-Hastings log ratio (Eq. (13) with the proposal density) falls below log u by
+ * more than beta_0 * margin is rejected there, and every other one is evaluated by the
+ * second likelihood (lisa_sampler_set_flow_likelihood), whose ln L decides it and is the
+ * one stored on acceptance.  The chain equals the unscreened chain of the second
+ * likelihood whenever the two likelihoods differ by less than margin at the rejected
+ * proposals (e.g. split precision against FP64: |d lnL| ~1e-4 near the posterior at SNR
+ * 1000), while the second likelihood works only on the proposals sent on.  Needs a
+ * second likelihood; LISA_ERR_STATE otherwise, LISA_ERR_ARG for a negative or
+ * non-finite margin. */
+lisa_status lisa_sampler_set_flow_screen(lisa_sampler_t *s, double margin);
+
+/* Flow proposals sent to the second likelihood by the screen since set_state. */
+lisa_status lisa_sampler_flow_screen_count(lisa_sampler_t *s, int64_t *sent);
+
 /* acc [2] = (accepted, proposed) flow moves since set_state; trainings so far; the last
  * minibatch loss of the last training (NaN before the first).  Any may be NULL. */
 lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings,

@@ -745,17 +745,45 @@ __global__ void __launch_bounds__(NTH) flow_propose_kernel(FlowView f, lisa_flow
 
 // Metropolis-Hastings acceptance of Eq. (13) with the tempered likelihood of the
 // coldest temperature and the prior
+// log of the MH ratio of flow proposal w with ln L ly (Eq. (13) with the proposal density)
+__device__ __forceinline__ double flow_log_ratio(const lisa_flowint::FStep &a, int w, double ly) {
+    const double beta = a.betas[0], py = a.fpy[w];
+    const double lt = beta > 0.0 ? __dmul_rn(beta, __dsub_rn(ly, a.lnl[w])) : 0.0;
+    return __dadd_rn(__dadd_rn(lt, __dsub_rn(py, a.lnp[w])), a.fq[w]);
+}
+
+// Screened flow moves: with the first likelihood's ln L, a proposal whose log ratio falls
+// below log u by more than beta margin is rejected here (a second likelihood within
+// margin of the first would reject it too); every other one, accepted or undecided, is
+// sent to the second likelihood, which decides it.  Proposals not sent on get a NaN
+// mass, so the second likelihood spends no dense work on them.
+__global__ void flow_screen_kernel(lisa_flowint::FStep a) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= a.W) return;
+    const lisa_smp::U4 q = lisa_smp::philox(*a.step, 4u, 0u, (uint32_t)w, a.k0, a.k1);
+    const double py = a.fpy[w];
+    const double lr = flow_log_ratio(a, w, a.fly[w]);
+    const double lu = log(lisa_smp::unit(q.v[0]));
+    const bool send = isfinite(py) && !(lu >= lr + a.betas[0] * a.margin);
+    a.fsent[w] = send ? 1 : 0;
+    for (int d = 0; d < FD; d++)
+        a.fpth2[(size_t)w * FD + d] = (send || d > 0) ? a.fpth[(size_t)w * FD + d] : NAN;
+    if (send) atomicAdd(a.facc + 2, 1ULL);
+}
+
 __global__ void flow_accept_kernel(lisa_flowint::FStep a) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= a.W) return;
     if (*a.err) return;
-    if (a.like_err && *a.like_err) {
+    if ((a.like_err && *a.like_err) || (a.like_err2 && *a.like_err2)) {
         atomicOr(a.err, 1);
         return;
     }
     if (w == 0) atomicAdd(a.facc + 1, (unsigned long long)a.W);
     const lisa_smp::U4 q = lisa_smp::philox(*a.step, 4u, 0u, (uint32_t)w, a.k0, a.k1);
-    const double beta = a.betas[0], py = a.fpy[w], ly = a.fly[w];
+    if (a.margin > 0.0 && !a.fsent[w]) return;  // rejected by the screen
+    const double beta = a.betas[0], py = a.fpy[w];
+    const double ly = a.margin > 0.0 ? a.fly2[w] : a.fly[w];
     const double lt = beta > 0.0 ? __dmul_rn(beta, __dsub_rn(ly, a.lnl[w])) : 0.0;
     const double lr = __dadd_rn(__dadd_rn(lt, __dsub_rn(py, a.lnp[w])), a.fq[w]);
     if (isfinite(py) && log(lisa_smp::unit(q.v[0])) < lr) {
@@ -871,6 +899,11 @@ namespace lisa_flowint {
 
 cudaError_t launch_flow_propose(lisa_flow_t *f, const FStep &a, cudaStream_t s) {
     flow_propose_kernel<<<(a.W + TS - 1) / TS, NTH, eval_smem(), s>>>(view(f), a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_screen(const FStep &a, cudaStream_t s) {
+    flow_screen_kernel<<<(a.W + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -24,13 +24,23 @@ struct FStep {
     double *fly;                // [W] their ln L (written by the likelihood or the test target)
     double *fq;                 // [W] log q(x) - log q(y)
     double *fpy;                // [W] ln prior of the proposals
-    unsigned long long *facc;   // [2] accepted, proposed
+    unsigned long long *facc;   // [3] accepted, proposed, sent to the second likelihood
     int *err;                   // sticky sampler error
     const int *like_err;        // the likelihood's flag of its last call (or NULL)
+    // Screened flow moves (margin > 0): the sampler's own likelihood evaluates every
+    // proposal (fly); those it rejects by more than margin in ln L keep that decision, the
+    // others are evaluated again by the second likelihood (fly2), which decides them.
+    double margin;
+    double *fpth2;              // [W][11] proposals sent on; the rest carry a NaN mass
+    double *fly2;               // [W] their ln L from the second likelihood
+    int *fsent;                 // [W] 1 if the proposal was sent on
+    const int *like_err2;       // the second likelihood's flag (or NULL)
 };
 
 cudaError_t launch_flow_propose(lisa_flow_t *f, const FStep &a, cudaStream_t s);
 cudaError_t launch_flow_accept(const FStep &a, cudaStream_t s);
+// screened flow moves: the first likelihood's verdict, and the proposals for the second
+cudaError_t launch_flow_screen(const FStep &a, cudaStream_t s);
 // training without host synchronisation (losses kept on the device)
 lisa_status flow_train_async(lisa_flow_t *f, const double *d_data, int64_t n, int iters,
                              int batch, double lr, uint64_t seed, uint32_t round, cudaStream_t s);

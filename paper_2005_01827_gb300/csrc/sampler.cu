@@ -326,7 +326,18 @@ lisa_status enqueue_step(lisa_sampler_t *s, bool with_flow, int *nl) {
     if (with_flow) {
         SCK(lisa_flowint::launch_flow_propose(s->flow, s->fst, s->stream), "flow proposal launch");
         count++;
-        if (s->dev.target == LISA_TARGET_LIKELIHOOD) {
+        if (s->dev.target == LISA_TARGET_LIKELIHOOD && s->flow_like && s->fst.margin > 0.0) {
+            // screened: the sampler's likelihood on every proposal, then the second
+            // likelihood on the ones the screen sends on
+            int l1 = 0, l2 = 0;
+            lisa_status st = lisa::like_enqueue(s->like, s->fst.fpth, s->fst.W, s->fst.fly, s->stream, &l1);
+            if (st != LISA_OK) return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->like));
+            SCK(lisa_flowint::launch_flow_screen(s->fst, s->stream), "flow screen launch");
+            st = lisa::like_enqueue(s->flow_like, s->fst.fpth2, s->fst.W, s->fst.fly2, s->stream, &l2);
+            if (st != LISA_OK)
+                return sfail(s, st, std::string("likelihood: ") + lisa_like_last_error(s->flow_like));
+            count += l1 + 1 + l2;
+        } else if (s->dev.target == LISA_TARGET_LIKELIHOOD) {
             int l = 0;
             lisa_like_t *fl = s->flow_like ? s->flow_like : s->like;
             lisa_status st = lisa::like_enqueue(fl, s->fst.fpth, s->fst.W, s->fst.fly, s->stream, &l);
@@ -599,7 +610,7 @@ lisa_status lisa_sampler_set_state(lisa_sampler_t *s, const double *x, uint32_t 
     SCK(cudaMemsetAsync(d.swaps, 0, sizeof(unsigned long long) * 2 * d.T, s->stream), "cudaMemsetAsync");
     SCK(cudaMemsetAsync(d.err, 0, sizeof(int), s->stream), "cudaMemsetAsync");
     if (s->flow_on)
-        SCK(cudaMemsetAsync(s->fst.facc, 0, sizeof(unsigned long long) * 2, s->stream), "cudaMemsetAsync");
+        SCK(cudaMemsetAsync(s->fst.facc, 0, sizeof(unsigned long long) * 3, s->stream), "cudaMemsetAsync");
     const int n = d.T * d.H;
     for (int c = 0; c < 2; c++) {
         init_kernel<<<blocks_for(n), kThreads, 0, s->stream>>>(d, c);
@@ -731,14 +742,14 @@ lisa_status lisa_sampler_enable_flow(lisa_sampler_t *s, const lisa_flow_schedule
     cudaError_t e;
     if ((e = salloc(s, &a.fy, W * D)) != cudaSuccess || (e = salloc(s, &a.fpth, W * D)) != cudaSuccess ||
         (e = salloc(s, &a.fly, W)) != cudaSuccess || (e = salloc(s, &a.fq, W)) != cudaSuccess ||
-        (e = salloc(s, &a.fpy, W)) != cudaSuccess || (e = salloc(s, &a.facc, 2)) != cudaSuccess)
+        (e = salloc(s, &a.fpy, W)) != cudaSuccess || (e = salloc(s, &a.facc, 3)) != cudaSuccess)
         return scuda(s, e, "device allocation (flow step)");
     if (fs->train_every > 0) {
         if ((e = salloc(s, &d.ring, (size_t)fs->train_every * W * D)) != cudaSuccess)
             return scuda(s, e, "device allocation (training ring)");
         d.ring_rows = fs->train_every;
     }
-    SCK(cudaMemsetAsync(a.facc, 0, sizeof(unsigned long long) * 2, s->stream), "cudaMemsetAsync");
+    SCK(cudaMemsetAsync(a.facc, 0, sizeof(unsigned long long) * 3, s->stream), "cudaMemsetAsync");
     a.W = d.W;
     a.k0 = d.k0;
     a.k1 = d.k1;
@@ -778,13 +789,46 @@ lisa_status lisa_sampler_set_flow_likelihood(lisa_sampler_t *s, lisa_like_t *lik
         if (li2.device != s->device) return sfail(s, LISA_ERR_ARG, "the flow's likelihood is on another device");
         if (li2.max_batch < s->dev.W) return sfail(s, LISA_ERR_ARG, "the flow's likelihood needs max_batch >= n_walkers");
         if (li2.t0 != s->li.t0) return sfail(s, LISA_ERR_ARG, "the flow's likelihood has another t0");
-        s->fst.like_err = li2.err_flag;
+        s->fst.like_err = s->fst.margin > 0.0 ? s->li.err_flag : li2.err_flag;
+        s->fst.like_err2 = s->fst.margin > 0.0 ? li2.err_flag : nullptr;
     } else {
         s->fst.like_err = s->li.err_flag;
+        s->fst.like_err2 = nullptr;
+        s->fst.margin = 0.0;
     }
     s->flow_like = like2;
     drop_graph(s);
     return LISA_OK;
+}
+
+lisa_status lisa_sampler_set_flow_screen(lisa_sampler_t *s, double margin) {
+    if (!s) return LISA_ERR_ARG;
+    if (!s->flow_on || !s->flow_like)
+        return sfail(s, LISA_ERR_STATE, "set the flow's second likelihood first");
+    if (!(margin >= 0.0) || !std::isfinite(margin)) return sfail(s, LISA_ERR_ARG, "margin must be finite and >= 0");
+    lisa_flowint::FStep &a = s->fst;
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (margin > 0.0 && !a.fpth2) {
+        const size_t W = s->dev.W;
+        cudaError_t e;
+        if ((e = salloc(s, &a.fpth2, W * D)) != cudaSuccess || (e = salloc(s, &a.fly2, W)) != cudaSuccess ||
+            (e = salloc(s, &a.fsent, W)) != cudaSuccess)
+            return scuda(s, e, "device allocation (flow screen)");
+    }
+    const lisa::LikeInfo li2 = lisa::like_info(s->flow_like);
+    a.margin = margin;
+    a.like_err = margin > 0.0 ? s->li.err_flag : li2.err_flag;
+    a.like_err2 = margin > 0.0 ? li2.err_flag : nullptr;
+    drop_graph(s);
+    return LISA_OK;
+}
+
+lisa_status lisa_sampler_flow_screen_count(lisa_sampler_t *s, int64_t *sent) {
+    if (!s || !sent) return LISA_ERR_ARG;
+    if (!s->flow_on) return sfail(s, LISA_ERR_STATE, "the flow is not enabled");
+    SCK(cudaSetDevice(s->device), "cudaSetDevice");
+    SCK(cudaMemcpyAsync(sent, s->fst.facc + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream), "download");
+    return wait_done(s, s->timeout_s);
 }
 
 lisa_status lisa_sampler_flow_stats(lisa_sampler_t *s, int64_t *acc, int *trainings, double *last_loss) {

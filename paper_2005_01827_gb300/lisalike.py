@@ -40,6 +40,7 @@ SYMBOLS = (
     "lisa_sampler_sky_mode_init",
     "lisa_autocorr_time", "lisa_flow_default_schedule", "lisa_sampler_enable_flow",
     "lisa_sampler_get_flow", "lisa_sampler_flow_stats", "lisa_sampler_set_flow_likelihood",
+    "lisa_sampler_set_flow_screen", "lisa_sampler_flow_screen_count",
     # include/lisa_probe.h
     "lisa_probe_pipes",
     # include/lisa_flow.h
@@ -209,6 +210,10 @@ def load(path: str = LIB_PATH):
     L.lisa_sampler_flow_stats.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
     L.lisa_sampler_set_flow_likelihood.argtypes = [vp, vp]
     L.lisa_sampler_set_flow_likelihood.restype = i
+    L.lisa_sampler_set_flow_screen.argtypes = [vp, d]
+    L.lisa_sampler_set_flow_screen.restype = i
+    L.lisa_sampler_flow_screen_count.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.lisa_sampler_flow_screen_count.restype = i
     L.lisa_flow_create.argtypes = [u64, C.POINTER(vp)]
     L.lisa_flow_destroy.argtypes = [vp]
     L.lisa_flow_destroy.restype = None
@@ -704,6 +709,17 @@ class LisaSampler:
         _scheck(load().lisa_sampler_set_flow_likelihood(self.h, None if like2 is None else like2.h),
                 self.h)
         self.flow_like = like2
+
+    def set_flow_screen(self, margin):
+        """Screen the flow moves with the sampler's own likelihood (margin in ln L; 0: off);
+        see lisa_sampler_set_flow_screen."""
+        _scheck(load().lisa_sampler_set_flow_screen(self.h, float(margin)), self.h)
+
+    def flow_screen_count(self):
+        """Flow proposals sent to the second likelihood since set_state."""
+        n = C.c_int64()
+        _scheck(load().lisa_sampler_flow_screen_count(self.h, C.byref(n)), self.h)
+        return n.value
 
     def flow_stats(self):
         acc = np.zeros(2, dtype=np.int64)

@@ -264,3 +264,68 @@ def test_flow_moves_with_an_fp64_likelihood_match_the_oracle(pkg, orc):
     like.close()
     like64.close()
     assert n_acc > 0 and n_bad <= 2
+
+
+def test_screened_flow_moves_equal_the_fp64_ones(pkg, orc):
+    """Flow moves screened by the split-precision likelihood (margin 0.05 in ln L) give the
+    same chain, bit for bit, as flow moves all evaluated by the FP64 handle: every
+    proposal the screen does not reject is decided on its FP64 ln L, and the ones it
+    rejects lie further below log u than the two precisions differ.  The FP64 handle then
+    evaluates only the proposals sent on."""
+    LL = pkg.lisalike
+    modes, K = [(2, 2), (3, 3)], 128
+    g = W.GRID_C1
+    S = orc.psd_aet(g.freqs())
+    inj = np.array(W.THETA_C1_Z)
+    inj[4] = orc.dl_gpc(inj[4])
+    inj[10] = 1000.0
+    d = orc.template(inj, W.T0_C1, modes, K, g.f0, g.df, g.n_bins)
+    d = d + orc.noise(S, g.df, W.white_noise(g.n_bins, 6))
+    xc = orc.from_physical(inj)
+    lo, hi = W.TABLE1_LOWER, W.TABLE1_UPPER
+    Wn, n_steps = 64, 8
+    rng = np.random.default_rng(3)
+    sig = np.array([1e-4, 1e-4, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-4, 1e-4, 1e-3, 1e-4])
+    x0 = xc + sig * rng.standard_normal((Wn, D))
+    like = pkg.LisaLike(modes=modes, n_knots=K, t0=W.T0_C1, max_batch=Wn, precision=1)
+    like.set_data(g.f0, g.df, g.n_bins, d, S)
+    like64 = pkg.LisaLike(modes=modes, n_knots=K, t0=W.T0_C1, max_batch=Wn, precision=0)
+    like64.set_data(g.f0, g.df, g.n_bins, d, S)
+    w = W.flow_init_weights(4, out_scale=0.05)
+
+    def make(screen):
+        s = LL.LisaSampler(like, n_temps=1, n_walkers=Wn, seed=13, lisa_frame=0, lower=lo,
+                           upper=hi)
+        fl = s.enable_flow(train_every=0, flow_only=1)
+        if screen:
+            with pytest.raises(LL.LisaError) as e:     # a screen needs a second likelihood
+                s.set_flow_screen(0.05)
+            assert e.value.status == LL.LISA_ERR_STATE
+        s.set_flow_likelihood(like64)
+        if screen:
+            with pytest.raises(LL.LisaError) as e:
+                s.set_flow_screen(-1.0)
+            assert e.value.status == LL.LISA_ERR_ARG
+            s.set_flow_screen(0.05)
+        fl.set_weights(w)
+        fl.set_whitening(xc, np.diag(1.5 * sig))
+        s.set_state(x0[None])
+        return s
+
+    a, b = make(False), make(True)
+    for _ in range(n_steps):
+        a.run(1)
+        b.run(1)
+        xa, la, _, _ = a.state()
+        xb, lb, _, _ = b.state()
+        assert np.array_equal(xa, xb) and np.array_equal(la, lb)
+    acc_a, acc_b = a.flow_stats()[0], b.flow_stats()[0]
+    sent = b.flow_screen_count()
+    print("screened flow moves: %d of %d proposals sent to the FP64 likelihood, %d accepted"
+          % (sent, n_steps * Wn, acc_b[0]))
+    assert np.array_equal(acc_a, acc_b) and acc_b[0] > 0
+    assert acc_b[0] <= sent < n_steps * Wn
+    a.close()
+    b.close()
+    like.close()
+    like64.close()
