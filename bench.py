@@ -947,11 +947,11 @@ def main():
     ap.add_argument("--flow-screen", type=float, default=0.05,
                     help="margin in ln L of the split-precision screen of the FP64 flow "
                          "moves (0: every flow proposal evaluated in FP64)")
-    ap.add_argument("--flow-burn", type=int, default=2000,
+    ap.add_argument("--flow-burn", type=int, default=6000,
                     help="burn-in steps of each arm of the flow-vs-plain part")
-    ap.add_argument("--flow-plain-steps", type=int, default=2500,
+    ap.add_argument("--flow-plain-steps", type=int, default=2000,
                     help="timed steps of the plain arm of the flow-vs-plain part")
-    ap.add_argument("--flow-steps", type=int, default=2500,
+    ap.add_argument("--flow-steps", type=int, default=2000,
                     help="timed steps of the flow arm of the flow-vs-plain part")
     args = ap.parse_args()
     world, rank, local = dist_init()
