@@ -62,7 +62,7 @@ BYTES_BIN = 72
 # a capture reports null.
 TRAFFIC_F64_PER_WALKER_BIN = {(8, 8): (753.79e6 + 5.11e6) / 69589136,
                               (4, 8): (755.36e6 + 6.43e6) / 69589136}
-TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (374.29e6 + 4.62e6) / 69589136}
+TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (374.22e6 + 4.57e6) / 69589136}
 
 
 def peaks():
