@@ -5,10 +5,13 @@
 //
 // Phase: per spline segment an FP64 prologue turns the cubic phase (including the
 // -2 pi f t_coal ramp) into forward differences over one bin, Phi, D1, D2, D3, held as
-// 64-bit fixed-point fractions of a turn.  Per bin the phase then advances by three
-// exact modular integer additions, so no rounding accumulates along a segment; its top
-// 8 bits index a table of e^{2 pi i k / 256} and the next 23 bits give a small angle
-// (< 2 pi / 256) whose sine and cosine are short FP32 polynomials.
+// 64-bit fixed-point fractions of a turn (with extra low words for the differences).
+// Each thread moves them to the first bin of its 8-bin chunk by Newton's formula in
+// modular integer arithmetic, so no rounding accumulates along a segment, rounds them
+// to 32-bit words and advances the phase by three 32-bit additions per bin; the top 8
+// bits of the phase index a table of e^{2 pi i k / 256} (the nearest entry) and the
+// next 23 bits give a small signed angle (|r| <= pi / 256) whose sine and cosine are
+// short FP32 polynomials.
 //
 // Packed FP32: each channel's (Re, Im) transfer pair is one Horner evaluation in
 // Blackwell's f32x2 FMA (one instruction for both lanes, each rounded as the scalar
@@ -155,8 +158,9 @@ __global__ void __launch_bounds__(256) segprep_kernel(StageDims d, StageBufs b, 
             r.pad[0] = r.pad[1] = 0;
             if (s == 0) {  // the (walker, mode)'s segment-guess constants, read once per tile
                 const double f_lo = b.fedge[2 * wm], f_hi = b.fedge[2 * wm + 1];
-                r.pad[0] = __float_as_int((float)f_lo);
-                r.pad[1] = __float_as_int((float)((double)(K - 1) / log2(f_hi / f_lo)));
+                const double scl = (double)(K - 1) / log2(f_hi / f_lo);
+                r.pad[0] = __float_as_int((float)(log2(f_lo) * scl));
+                r.pad[1] = __float_as_int((float)scl);
             }
             segs[g] = r;
         } else {
@@ -183,11 +187,16 @@ cudaError_t launch_phaseprep(const StageDims &d, const StageBufs &b, unsigned lo
 }
 
 // ------------------------------------------------------------------------ dense
-// segment of bin j from the log spacing of the knots (MUFU log2 guess), then moved by
-// the integer knot-to-bin boundaries so that kb[s] <= j < kb[s + 1]
+// segment of bin j from the log spacing of the knots: (log2 f - log2 f_lo) (K - 1) /
+// log2(f_hi / f_lo) by one MUFU log2 and one FMA (l0 = scale log2 f_lo)
+__device__ __forceinline__ int seg_index_guess(float fjf, float l0, float scale) {
+    return (int)fmaf(__log2f(fjf), scale, -l0);
+}
+
+// the guess moved by the integer knot-to-bin boundaries so that kb[s] <= j < kb[s + 1]
 __device__ __forceinline__ int seg_guess(const int *__restrict__ kb, int K, int j, float fjf,
-                                         float flo, float scale) {
-    int s = (int)(__log2f(__fdividef(fjf, flo)) * scale);
+                                         float l0, float scale) {
+    int s = seg_index_guess(fjf, l0, scale);
     s = min(max(s, 0), K - 2);
     while (s > 0 && __ldg(kb + s) > j) s--;
     while (s < K - 2 && __ldg(kb + s + 1) <= j) s++;
@@ -229,9 +238,16 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 }
 #undef LISA_F32X2
 
+// phase and forward differences at one bin as 32-bit fractions of a turn; the phase is
+// offset by half a table cell so that its top 8 bits name the nearest table entry
 struct PhaseState {
-    unsigned long long ph, d1, d2, d3;
+    unsigned int ph, d1, d2, d3;
 };
+
+// x / 2^32 rounded to the nearest integer (modulo 2^32)
+__device__ __forceinline__ unsigned int top_rn(unsigned long long x) {
+    return (unsigned int)(x >> 32) + ((unsigned int)x >> 31);
+}
 
 // floor(c L / 2^64) from the top 32 bits of L: low by less than c / 2^32 + 2 (c < 2^63)
 __device__ __forceinline__ unsigned long long mulhi_top32(unsigned long long c,
@@ -243,8 +259,11 @@ __device__ __forceinline__ unsigned long long mulhi_top32(unsigned long long c,
 // forward differences of the segment's phase moved from its first bin to bin n >= 0
 // (Newton's forward-difference formula in modular integer arithmetic).  The carries of
 // the low words into the phase and the first difference are taken from their top 32
-// bits and the ones multiplied by n are dropped: the anchor is low by at most a few n
-// units of 2^-64 turn, below 2^-38 turn along any chunk for n < 2^21.
+// bits and the ones multiplied by n are dropped: the 64-bit anchor is low by at most a
+// few n units of 2^-64 turn for n < 2^21.  It is then rounded to 32-bit words, with
+// which a thread advances its chunk: after i steps the phase is off by at most
+// (1 + i + i(i-1)/2 + i(i-1)(i-2)/6) / 2 units of 2^-32 turn (32 units, 4.7e-8 rad, at
+// i = 7), and every chunk starts again from the exact record.
 __device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, int n) {
     const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(rp->ph);
     const ulonglong2 a = __ldg(w), b = __ldg(w + 1);
@@ -253,16 +272,18 @@ __device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, in
     // is a multiple of 3: multiplying by the inverse of 3 modulo 2^64 divides it exactly)
     const unsigned long long c2 = ((unsigned long long)un * (un - 1u)) >> 1;
     const unsigned long long c3 = (c2 * (unsigned long long)(un - 2u)) * 0xAAAAAAAAAAAAAAABull;
-    PhaseState p;
-    p.ph = a.x + a.y * un + c2 * b.x + c3 * b.y;
-    p.d1 = a.y + b.x * un + c2 * b.y;
-    p.d2 = b.x + b.y * un;
-    p.d3 = b.y;
+    unsigned long long ph = a.x + a.y * un + c2 * b.x + c3 * b.y;
+    unsigned long long d1 = a.y + b.x * un + c2 * b.y;
     if (n >= 2) {
         const ulonglong2 c = __ldg(w + 2), e = __ldg(w + 3);
-        p.ph += mulhi_top32(c2, c.y) + mulhi_top32(c3, e.x);
-        p.d1 += mulhi_top32(c2, e.x);
+        ph += mulhi_top32(c2, c.y) + mulhi_top32(c3, e.x);
+        d1 += mulhi_top32(c2, e.x);
     }
+    PhaseState p;
+    p.ph = top_rn(ph) + (1u << 23);  // + half a cell of the 256-entry table
+    p.d1 = top_rn(d1);
+    p.d2 = top_rn(b.x + b.y * un);
+    p.d3 = top_rn(b.y);
     return p;
 }
 
@@ -289,19 +310,21 @@ __device__ __forceinline__ SegCoef seg_coef(const SegRec *__restrict__ rp) {
     return r;
 }
 
-// e^{2 pi i ph / 2^64}: table entry of the top 8 bits times a short polynomial in the
-// next 23 bits (angle below 2 pi / 256)
-__device__ __forceinline__ void phasor(unsigned long long ph, const float2 *__restrict__ tab,
+// e^{2 pi i (ph - 2^23) / 2^32} for a phase word ph offset by half a cell: the table
+// entry k = ph >> 24 (the nearest multiple of 2 pi / 256) times the rotation by the
+// remaining signed angle r, |r| <= pi / 256, whose cosine 1 - r^2/2 is off by r^4/24 <
+// 1e-9 and sine r - r^3/6 by r^5/120 < 3e-12
+__device__ __forceinline__ void phasor(unsigned int ph, const float2 *__restrict__ tab,
                                        float &zr, float &zi) {
-    const unsigned int hi = (unsigned int)(ph >> 32);
-    const float2 t = tab[hi >> 24];
-    // x in [1, 2) carries the next 23 bits; fmaf(x, step, -step) = (x - 1) step rounded
-    // once, as (x - 1) is exact
-    const float x = __uint_as_float(0x3f800000u | ((hi << 8) >> 9));
-    const float r = fmaf(x, 0.024543692606170259f, -0.024543692606170259f);  // 2 pi / 256
+    const float2 t = tab[ph >> 24];
+    // x = 1 + (ph mod 2^24) / 2^24 from the next 23 bits; x - 1.5 is exact, and so is
+    // 1.5 kStep (kStep is 2 pi / 256 rounded to 23 significant bits), so the FMA
+    // rounds (x - 1.5) kStep once
+    const float x = __uint_as_float(0x3f800000u | ((ph << 8) >> 9));
+    const float r = fmaf(x, 0.02454369142651558f, -0.03681553713977337f);
     const float r2 = r * r;
     const float sn = r * fmaf(r2, -0.16666666666666666f, 1.0f);
-    const float cs = fmaf(r2, fmaf(r2, 0.041666666666666664f, -0.5f), 1.0f);
+    const float cs = fmaf(r2, -0.5f, 1.0f);
     zr = t.x * cs - t.y * sn;
     zi = fmaf(t.x, sn, t.y * cs);
 }
@@ -426,7 +449,7 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
             const int k = tid / kMaxModes, mi = tid % kMaxModes;
             const int i = g * G + k;
             int lo = 1, hi = 0;
-            float flo = 1.0f, scl = 0.0f;
+            float flo = 0.0f, scl = 0.0f;  // scale log2 f_lo and the guess scale
             if (i < d.B && mi < d.L) {
                 const int w = b.order[i];
                 const size_t wm = (size_t)w * d.L + mi;
@@ -475,8 +498,7 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 const size_t wm = (size_t)w * d.L + mi;
                 const int *kb = b.kb + wm * K;
                 const SegRec *sg = segs + wm * (K - 1);
-                int s = (int)(__log2f(__fdividef(fmaf((float)ja, dff, f0f), s_flo[k][mi])) *
-                              s_scl[k][mi]);
+                int s = seg_index_guess(fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
                 s = min(max(s, 0), K - 2);
                 SegCoef r = seg_coef(sg + s);
                 int knext = (int)__ldg(&sg[s].ph[7]);

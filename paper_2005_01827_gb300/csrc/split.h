@@ -16,7 +16,8 @@ constexpr int kBinFloats = 9;
 // A 2^64, and for channel x = 0, 1, 2 (A, E, T) c[4 + 8 x + 2 k] and c[4 + 8 x + 2 k + 1]
 // are the t^k coefficients of Re T^X and Im T^X, interleaved so that the pair is one
 // packed f32x2 operand.  ph[] is the fixed-point phase record of the segment (see
-// kernels.h).
+// kernels.h).  pad[] is zero except in segment 0, where it holds the FP32 bit patterns
+// of the segment-guess constants: sc log2 f_lo and sc = (K - 1) / log2(f_hi / f_lo).
 struct __align__(16) SegRec {
     float c[28];
     unsigned long long ph[kPhaseWords];
