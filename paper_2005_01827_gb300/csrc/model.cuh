@@ -376,6 +376,23 @@ __device__ inline double delay_phase(const Frame &fr, double f, double t) {
 // sinc argument differs.  The constellation of constellation() is rigid: every arm
 // q_c - q_a has length L exactly (to rounding), so the unit vector is (q_c - q_a) / L;
 // the two sinc quotients of an arm share one division.
+//
+// Six sincos instead of eleven, by angle addition (every identity exact in real
+// arithmetic):
+//  * x = pi f L: sincos(x) gives the delay operator D = e^{-2ix} and the common factor
+//    e^{-ix} of the arms' propagation phases e^{-i pi f (L + k.(q_a + q_c))};
+//  * the sinc arguments x (1 -+ k.n) take sin(x) and sincos(x k.n): sin(x (1 -+ k.n)) =
+//    sin x cos(x k.n) -+ cos x sin(x k.n), used where 1 -+ k.n >= 1e-3 (there the
+//    identity loses at most 1e-13 relative); closer to an arm the direct sine is taken;
+//  * the arms (0,1), (0,2), (1,2) have n_02 = n_01 + n_12, so the middle arm's x k.n
+//    and its sincos come from the other two; and q_0 + q_1 + q_2 = 0 gives
+//    k.(q_0 + q_2) = -k.(q_0 + q_1) - k.(q_1 + q_2), so its propagation phase is the
+//    conjugate product of the other two.
+__device__ inline double link_sin(double a, double sx, double cx, double sy, double cy,
+                                  double sgn, double gap) {
+    return gap >= 1e-3 ? sx * cy + sgn * cx * sy : sin(a);
+}
+
 __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f, double t,
                                     cplx out[3], double *delay) {
     double p0[3], q[3][3];
@@ -383,8 +400,11 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
     if (delay) *delay = -kTwoPi * f * (fr.k[0] * p0[0] + fr.k[1] * p0[1] + fr.k[2] * p0[2]);
     const double L = kArmM / kClight;
     const double pfl = kPi * f * L;
-    cplx y[3][3];  // y[emitter][receiver]
+    double sp, cp;
+    sincos(pfl, &sp, &cp);
     const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    double kn[3], kq[3];
+    cplx F[3];
 #pragma unroll
     for (int e = 0; e < 3; e++) {
         const int a = pa[e], c = pb[e];
@@ -392,12 +412,12 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
         const double inv = 1.0 / L;
 #pragma unroll
         for (int i = 0; i < 3; i++) n[i] = q[c][i] - q[a][i];
-        double kn = 0.0, kq = 0.0, xp = 0.0, xc = 0.0;
+        double kne = 0.0, kqe = 0.0, xp = 0.0, xc = 0.0;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             n[i] *= inv;
-            kn += fr.k[i] * n[i];
-            kq += fr.k[i] * (q[a][i] + q[c][i]);
+            kne += fr.k[i] * n[i];
+            kqe += fr.k[i] * (q[a][i] + q[c][i]);
         }
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -410,15 +430,43 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
             xp += n[i] * tp;
             xc += n[i] * tcx;
         }
-        const cplx F = {kp.re * xp + kc.re * xc, kp.im * xp + kc.im * xc};
-        const cplx eF = cmul(cexpi(-kPi * f * (L + kq)), F);
-        const double a1 = pfl * (1.0 - kn), a2 = pfl * (1.0 + kn);  // a -> c and c -> a
+        kn[e] = kne;
+        kq[e] = kqe;
+        F[e] = {kp.re * xp + kc.re * xc, kp.im * xp + kc.im * xc};
+    }
+    // the middle arm's k.n from the outer two (n_02 = n_01 + n_12)
+    kn[1] = kn[0] + kn[2];
+    // e^{-i pi f k.(q_a + q_c)} of the outer arms, the middle one's as their conjugate product
+    cplx g[3];
+    {
+        double s0, c0, s2, c2;
+        sincos(kPi * f * kq[0], &s0, &c0);
+        sincos(kPi * f * kq[2], &s2, &c2);
+        g[0] = {c0, -s0};
+        g[2] = {c2, -s2};
+        const cplx g02 = cmul(g[0], g[2]);
+        g[1] = {g02.re, -g02.im};
+    }
+    // sincos(x k.n) of the outer arms, the middle one's by angle addition
+    double sn[3], cn[3];
+    sincos(pfl * kn[0], &sn[0], &cn[0]);
+    sincos(pfl * kn[2], &sn[2], &cn[2]);
+    sn[1] = sn[0] * cn[2] + cn[0] * sn[2];
+    cn[1] = cn[0] * cn[2] - sn[0] * sn[2];
+    const cplx ex = {cp, -sp};  // e^{-ix}
+    cplx y[3][3];  // y[emitter][receiver]
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const int a = pa[e], c = pb[e];
+        const cplx eF = cmul(cmul(ex, g[e]), F[e]);
+        const double g1 = 1.0 - kn[e], g2 = 1.0 + kn[e];
+        const double a1 = pfl * g1, a2 = pfl * g2;  // a -> c and c -> a
         double s1, s2;
         const double a12 = a1 * a2;
         if (a12 != 0.0) {
             const double r = 1.0 / a12;
-            s1 = sin(a1) * (a2 * r);
-            s2 = sin(a2) * (a1 * r);
+            s1 = link_sin(a1, sp, cp, sn[e], cn[e], -1.0, g1) * (a2 * r);
+            s2 = link_sin(a2, sp, cp, sn[e], cn[e], 1.0, g2) * (a1 * r);
         } else {
             s1 = (a1 == 0.0) ? 1.0 : sin(a1) / a1;
             s2 = (a2 == 0.0) ? 1.0 : sin(a2) / a2;
@@ -427,7 +475,7 @@ __device__ inline void tdi_transfer(const Frame &fr, cplx kp, cplx kc, double f,
         y[a][c] = {pfl * s1 * eF.im, -pfl * s1 * eF.re};
         y[c][a] = {pfl * s2 * eF.im, -pfl * s2 * eF.re};
     }
-    const cplx D = cexpi(-kTwoPi * f * L);
+    const cplx D = {cp * cp - sp * sp, -2.0 * sp * cp};  // e^{-2ix}
     const cplx D2 = cmul(D, D);
     const cplx fac = {1.0 - D2.re, -D2.im};
     const cplx X = cmul(fac, csub(cadd(y[2][0], cmul(D, y[0][2])), cadd(y[1][0], cmul(D, y[0][1]))));
