@@ -256,6 +256,20 @@ __device__ __forceinline__ unsigned long long mulhi_top32(unsigned long long c,
     return (c >> 32) * lh + (((unsigned long long)(unsigned int)c * lh) >> 32);
 }
 
+// the fixed-point phase words of a segment record (the last one holds the next
+// segment's first bin), loaded together with its cubics so that one round trip to
+// memory serves a guessed segment
+struct SegPhase {
+    ulonglong2 a, b, c, e;
+};
+
+__device__ __forceinline__ SegPhase seg_phase(const SegRec *__restrict__ rp) {
+    const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(rp->ph);
+    return SegPhase{__ldg(w), __ldg(w + 1), __ldg(w + 2), __ldg(w + 3)};
+}
+
+__device__ __forceinline__ int seg_next(const SegPhase &q) { return (int)(unsigned int)q.e.y; }
+
 // forward differences of the segment's phase moved from its first bin to bin n >= 0
 // (Newton's forward-difference formula in modular integer arithmetic).  The carries of
 // the low words into the phase and the first difference are taken from their top 32
@@ -264,9 +278,8 @@ __device__ __forceinline__ unsigned long long mulhi_top32(unsigned long long c,
 // which a thread advances its chunk: after i steps the phase is off by at most
 // (1 + i + i(i-1)/2 + i(i-1)(i-2)/6) / 2 units of 2^-32 turn (32 units, 4.7e-8 rad, at
 // i = 7), and every chunk starts again from the exact record.
-__device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, int n) {
-    const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(rp->ph);
-    const ulonglong2 a = __ldg(w), b = __ldg(w + 1);
+__device__ __forceinline__ PhaseState phase_at(const SegPhase &q, int n) {
+    const ulonglong2 a = q.a, b = q.b;
     const unsigned int un = (unsigned int)n;
     // n(n-1)/2 and n(n-1)(n-2)/6 (the product of three consecutive integers divided by 2
     // is a multiple of 3: multiplying by the inverse of 3 modulo 2^64 divides it exactly)
@@ -275,9 +288,8 @@ __device__ __forceinline__ PhaseState phase_at(const SegRec *__restrict__ rp, in
     unsigned long long ph = a.x + a.y * un + c2 * b.x + c3 * b.y;
     unsigned long long d1 = a.y + b.x * un + c2 * b.y;
     if (n >= 2) {
-        const ulonglong2 c = __ldg(w + 2), e = __ldg(w + 3);
-        ph += mulhi_top32(c2, c.y) + mulhi_top32(c3, e.x);
-        d1 += mulhi_top32(c2, e.x);
+        ph += mulhi_top32(c2, q.c.y) + mulhi_top32(c3, q.e.x);
+        d1 += mulhi_top32(c2, q.e.x);
     }
     PhaseState p;
     p.ph = top_rn(ph) + (1u << 23);  // + half a cell of the 256-entry table
@@ -501,15 +513,17 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                 int s = seg_index_guess(fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
                 s = min(max(s, 0), K - 2);
                 SegCoef r = seg_coef(sg + s);
-                int knext = (int)__ldg(&sg[s].ph[7]);
+                SegPhase q = seg_phase(sg + s);
+                int knext = seg_next(q);
                 // the record of the guessed segment is loaded with the bounds that check it,
                 // so a right guess (the usual case) costs no dependent load
                 if ((s > 0 && r.kb0 > ja) || knext <= ja) {  // the guess missed: search
                     s = seg_guess(kb, K, ja, fmaf((float)ja, dff, f0f), s_flo[k][mi], s_scl[k][mi]);
                     r = seg_coef(sg + s);
-                    knext = (int)__ldg(&sg[s].ph[7]);
+                    q = seg_phase(sg + s);
+                    knext = seg_next(q);
                 }
-                PhaseState p = phase_at(sg + s, ja - r.kb0);
+                PhaseState p = phase_at(q, ja - r.kb0);
                 const float ta = (float)(ja - r.kb0) * r.invw;
                 float2 tt = make_float2(ta, ta);  // (t, t): the packed Horner operand
                 if (ja == j0 && jb == j0 + C && knext >= j0 + C) {
@@ -534,8 +548,9 @@ __global__ void __launch_bounds__(128, 4) dense_split_kernel(StageDims d, StageB
                     if (j >= knext) {  // the chunk crosses into the next segment
                         s++;
                         r = seg_coef(sg + s);
-                        knext = (int)__ldg(&sg[s].ph[7]);
-                        p = phase_at(sg + s, j - r.kb0);
+                        q = seg_phase(sg + s);
+                        knext = seg_next(q);
+                        p = phase_at(q, j - r.kb0);
                         const float tj = (float)(j - r.kb0) * r.invw;
                         tt = make_float2(tj, tj);
                     }
