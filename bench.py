@@ -62,7 +62,7 @@ BYTES_BIN = 72
 # a capture reports null.
 TRAFFIC_F64_PER_WALKER_BIN = {(8, 8): (753.79e6 + 5.11e6) / 69589136,
                               (4, 8): (755.36e6 + 6.43e6) / 69589136}
-TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (374.19e6 + 4.64e6) / 69589136}
+TRAFFIC_SPLIT_PER_WALKER_BIN = {(8, 8): (374.96e6 + 4.37e6) / 69589136}
 
 
 def peaks():
@@ -343,9 +343,9 @@ def time_split(lisalike, LisaLike, g, th, B, args, world, stream, mode_bins, bin
                              "hbm": (tpw * bins / (dense_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"])
                              if (tpw and peaks().get("hbm_gbs")) else None,
                              "note": "fp64: per-item set-up only; mufu: one log2 per chunk "
-                                     "(the phasor is a table and polynomials); ncu: issue 62 %, "
-                                     "FMA pipe 51 % of cycles (packed f32x2 Horner and "
-                                     "integrand), ALU 32 %"},
+                                     "(the phasor is a table and polynomials); ncu: issue 65 %, "
+                                     "FMA pipe 54 % of cycles (packed f32x2 Horner and "
+                                     "integrand), ALU 29 %"},
                          "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
                          "measured_pipes": {
                              "fp32_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
